@@ -1,0 +1,183 @@
+"""FP64 CPU oracle of the two-species soft-glassy lattice Boltzmann step.
+
+TEST INFRASTRUCTURE ONLY.  This package is the correctness reference for the
+CUDA path (Benzi et al., arXiv:0906.3611, Sec. II: Eq. (be), Eq. (FORCE),
+Eq. (PSI), Table I).  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import it.  It
+shares no code with the product package and does not import it.
+
+The arithmetic lives in ``lb_oracle.c`` (plain C, FP64, separate
+whole-lattice passes); this module compiles it with gcc and wraps it with
+ctypes.  ``theory.py`` holds the paper's closed forms and root-finders used
+as pins.  Every function here is pinned by ``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lb_oracle.c")
+_LIB = os.path.join(_HERE, "liblb_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+PERIODIC = 0
+COUETTE = 1
+INIT_UNIFORM_NOISE = 0
+INIT_BERNOULLI = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile ``lb_oracle.c`` into ``liblb_oracle.so`` next to it."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-o", _LIB + ".tmp", _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        build()
+        lib = ctypes.CDLL(_LIB)
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        lib.lbo_tables.argtypes = [ip, ip, dp, ip, ip, dp, dp]
+        lib.lbo_tables.restype = None
+        lib.lbo_densities.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp]
+        lib.lbo_densities.restype = None
+        lib.lbo_forces.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, dp]
+        lib.lbo_forces.restype = None
+        lib.lbo_step.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_long, ctypes.c_int]
+        lib.lbo_step.restype = ctypes.c_long
+        lib.lbo_observables.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp]
+        lib.lbo_observables.restype = ctypes.c_long
+        lib.lbo_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        lib.lbo_philox4x32_10.restype = None
+        lib.lbo_init.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, dp]
+        lib.lbo_init.restype = None
+        lib.lbo_init_densities.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                           ctypes.c_int, dp, dp]
+        lib.lbo_init_densities.restype = None
+        lib.lbo_max_threads.argtypes = []
+        lib.lbo_max_threads.restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def params_vector(p: dict) -> np.ndarray:
+    """Pack a parameter dict into the oracle's parameter vector.
+
+    Keys: tau (pair), rho0, G_AB, Ga (pair), Gr (pair), boundary, U_wall.
+    """
+    tau = p.get("tau", (1.0, 1.0))
+    Ga = p.get("Ga", (0.0, 0.0))
+    Gr = p.get("Gr", (0.0, 0.0))
+    return np.array([tau[0], tau[1], p.get("rho0", 1.0), p.get("G_AB", 0.0),
+                     Ga[0], Ga[1], Gr[0], Gr[1], float(p.get("boundary", PERIODIC)),
+                     p.get("U_wall", 0.0)], dtype=np.float64)
+
+
+def tables():
+    """Return (cx9, cy9, w9, cxF, cyF, pF, wF) exactly as the oracle uses them."""
+    lib = _load()
+    cx9 = (ctypes.c_int * 9)(); cy9 = (ctypes.c_int * 9)(); w9 = (ctypes.c_double * 9)()
+    cxf = (ctypes.c_int * 25)(); cyf = (ctypes.c_int * 25)()
+    pf = (ctypes.c_double * 25)(); wf = (ctypes.c_double * 25)()
+    lib.lbo_tables(cx9, cy9, w9, cxf, cyf, pf, wf)
+    return (np.array(cx9[:]), np.array(cy9[:]), np.array(w9[:]), np.array(cxf[:]),
+            np.array(cyf[:]), np.array(pf[:]), np.array(wf[:]))
+
+
+def densities(f: np.ndarray) -> np.ndarray:
+    """rho[2, ny, nx] of a population array f[2, 9, ny, nx]."""
+    lib = _load()
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    _, _, ny, nx = f.shape
+    rho = np.empty((2, ny, nx))
+    lib.lbo_densities(_dp(f), nx, ny, _dp(rho))
+    return rho
+
+
+def forces(rho: np.ndarray, p: dict) -> np.ndarray:
+    """F[2 species, 2 comps, ny, nx] of density fields rho[2, ny, nx], Eq. (FORCE)."""
+    lib = _load()
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    _, ny, nx = rho.shape
+    F = np.empty((2, 2, ny, nx))
+    lib.lbo_forces(_dp(rho), nx, ny, _dp(params_vector(p)), _dp(F))
+    return F
+
+
+def step(f: np.ndarray, p: dict, nsteps: int = 1, threads: int = 0):
+    """Advance a copy of f[2, 9, ny, nx] by nsteps; returns (f_new, bad_count)."""
+    lib = _load()
+    g = np.array(f, dtype=np.float64, order="C", copy=True)
+    _, _, ny, nx = g.shape
+    bad = lib.lbo_step(_dp(g), nx, ny, _dp(params_vector(p)), int(nsteps), int(threads))
+    if bad < 0:
+        raise MemoryError("oracle step: allocation failed")
+    return g, int(bad)
+
+
+def observables(f: np.ndarray, p: dict) -> dict:
+    """rho[2,ny,nx], u[2,ny,nx], stress[3], mass[4] of a state (see lb_oracle.c)."""
+    lib = _load()
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    _, _, ny, nx = f.shape
+    rho = np.empty((2, ny, nx)); u = np.empty((2, ny, nx))
+    stress = np.empty(3); mass = np.empty(4)
+    bad = lib.lbo_observables(_dp(f), nx, ny, _dp(params_vector(p)), _dp(rho), _dp(u),
+                              _dp(stress), _dp(mass))
+    if bad < 0:
+        raise MemoryError("oracle observables: allocation failed")
+    return {"rho": rho, "u": u, "stress": stress, "mass": mass, "bad": int(bad)}
+
+
+def philox4x32_10(ctr, key):
+    """One Philox4x32-10 block: four 32-bit counter words, two key words."""
+    lib = _load()
+    c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib.lbo_philox4x32_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def init_state(nx: int, ny: int, seed: int, kind: int, init) -> np.ndarray:
+    """Seeded initial populations f = w_i rho_s (zero velocity)."""
+    lib = _load()
+    f = np.empty((2, 9, ny, nx))
+    iv = np.zeros(6)
+    iv[: len(init)] = init
+    lib.lbo_init(_dp(f), nx, ny, ctypes.c_uint64(seed), int(kind), _dp(iv))
+    return f
+
+
+def init_densities(nx: int, ny: int, seed: int, kind: int, init) -> np.ndarray:
+    lib = _load()
+    rho = np.empty((2, ny, nx))
+    iv = np.zeros(6)
+    iv[: len(init)] = init
+    lib.lbo_init_densities(nx, ny, ctypes.c_uint64(seed), int(kind), _dp(iv), _dp(rho))
+    return rho
+
+
+def max_threads() -> int:
+    return int(_load().lbo_max_threads())
