@@ -1,0 +1,291 @@
+"""Throughput benchmark of the fused two-species lattice Boltzmann step.
+
+Default workload (one GPU): 4096 x 4096 Couette lattice, walls at +-U with
+U = 0.02, FP32 populations, seeded Bernoulli(0.7) droplet mixture, the
+rho0 = 0.7 couplings (G_AB = 0.405, G^a = -9, G^r = 8.1), tau = 1.  A step is
+one lb_step of the whole lattice (all 2 x 2^24 site updates); the metric is
+MLUPS (million two-species site updates per second).  Each population buffer
+is 1.21 GB, far larger than the 129 MB L2, so no flush is needed between steps.
+
+Multi-GPU (torchrun): independent replicas, one lattice per rank (weak
+scaling, no data-path collective); value = all ranks' site updates / the
+slowest rank's time.
+
+--impl reference times the FP64 CPU oracle instead (the baseline arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+PHYS = dict(tau=(1.0, 1.0), rho0=0.7, G_AB=0.405, Ga=(-9.0, -9.0), Gr=(8.1, 8.1))
+INIT = (0.7, 1.2, 0.1, 0.02)
+WORKLOADS = {
+    # name: (nx, ny, boundary, U, storage)
+    "couette4096_f32": (4096, 4096, 1, 0.02, 1),
+    "emulsion1024_f32": (1024, 1024, 0, 0.0, 1),
+    "couette4096_bf16dev": (4096, 4096, 1, 0.02, 2),
+    "couette4096_f16dev": (4096, 4096, 1, 0.02, 3),
+}
+STORAGE_NAME = {0: "f64", 1: "f32", 2: "bf16dev", 3: "f16dev"}
+ELEM = {0: 8, 1: 4, 2: 2, 3: 2}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while work runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = [r.split(",") for r in self.tmp.read().strip().splitlines() if r.strip()]
+        self.tmp.close()
+        os.unlink(self.tmp.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [c.strip() for c in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_baseline_run(nx, ny, boundary, U, steps):
+    """Time the FP64 oracle (as it stands) on the host cores."""
+    import oracle
+    p = dict(PHYS, boundary=boundary, U_wall=U)
+    f = oracle.init_state(nx, ny, 0, oracle.INIT_BERNOULLI, INIT)
+    t0 = time.perf_counter()
+    oracle.step(f, p, steps)
+    dt = time.perf_counter() - t0
+    return nx * ny * steps / dt / 1e6, dt, oracle.max_threads()
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    nx, ny, boundary, U, storage = WORKLOADS[args.workload]
+    # each step: one oracle step of a 1024 x 1024 sample of the workload (same physics,
+    # boundary and initial recipe); bounded so the whole run takes a few minutes
+    sx = sy = 1024
+    import oracle
+    p = dict(PHYS, boundary=boundary, U_wall=U)
+    f = oracle.init_state(sx, sy, 0, oracle.INIT_BERNOULLI, INIT)
+    f, _ = oracle.step(f, p, args.warmup)
+    t0 = time.perf_counter()
+    f, _ = oracle.step(f, p, args.steps)
+    dt = time.perf_counter() - t0
+    mlups = sx * sy * args.steps / dt / 1e6
+    cores = oracle.max_threads()
+    sample = f"FP64 oracle, {sx}x{sy} sample of {args.workload} per step, OpenMP {cores} threads"
+    line = {"impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "nx": nx, "ny": ny, "sample_nx": sx,
+                       "sample_ny": sy},
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_0906_3611_gb300 import lb
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    nx, ny, boundary, U, storage = WORKLOADS[args.workload]
+    params = lb.make_params(**PHYS, boundary=boundary, U_wall=U, storage=storage,
+                            rho_ref=(0.87, 0.43), init_kind=lb.LB_INIT_BERNOULLI, init=INIT)
+    stream = torch.cuda.Stream()
+    lat = lb.Lattice(nx, ny, params, stream=stream)
+    lat.init_random(rank)
+    sites = nx * ny
+
+    def barrier():
+        torch.cuda.synchronize()
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(torch.cuda.current_device() if world == 1 else local)
+    sampler.start()
+    lat.step(args.warmup)
+    lat.sync()
+    barrier()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    lat.step(args.steps)
+    end.record(stream)
+    end.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = start.elapsed_time(end)
+    status = lat.status()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if pg is not None:
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * sites * args.steps / (ms_max * 1e-3) / 1e6
+
+    # end-to-end through the C ABI with host buffers: pinned host state -> device,
+    # K steps, FP64 observables back to the host
+    es = ELEM[storage]
+    host = torch.empty(2 * 9 * ny * nx * es, dtype=torch.uint8).pin_memory()
+    lb.lb_get_state_raw(lat.h, host.data_ptr())
+    mass = np.zeros(4)
+    stress = np.zeros(3)
+    barrier()
+    t0 = time.perf_counter()
+    lb.lb_set_state_raw(lat.h, host.data_ptr())
+    lb.lb_step(lat.h, args.steps)
+    lb.lb_observables(lat.h, None, None, stress, mass)
+    e2e_s = time.perf_counter() - t0
+    t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if pg is not None:
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    e2e_value = world * sites * args.steps / float(t.item()) / 1e6
+
+    bytes_per_site = 2 * 18 * es  # 18 populations read + 18 written
+    kernel_s = ms * 1e-3 / args.steps
+    achieved = bytes_per_site * sites / kernel_s / 1e9
+    peak, peak_kind = peaks()
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.txt")
+    if os.path.exists(prof):
+        for line in open(prof):
+            if line.startswith(f"{args.workload} ") and "kernel_sha=" in line:
+                parts = dict(kv.split("=", 1) for kv in line.split()[1:] if "=" in kv)
+                from paper_0906_3611_gb300 import build as _b
+                if parts.get("kernel_sha") == _b.kernel_sha():
+                    traffic = float(parts["bytes_per_launch"])
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cs = args.cpu_steps
+        mlups_cpu, dt_cpu, cores = cpu_baseline_run(nx, ny, boundary, U, cs)
+        cpu = {"value": mlups_cpu, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": f"FP64 oracle, full {nx}x{ny} lattice of this workload, {cs} steps "
+                         f"({dt_cpu:.1f} s), OpenMP {cores} threads"}
+    if rank == 0:
+        line = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if storage != 0 else "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "nx": nx, "ny": ny,
+                           "boundary": "couette" if boundary else "periodic", "U_wall": U,
+                           "storage": STORAGE_NAME[storage], "init": "bernoulli(0.7) droplets",
+                           "l2": f"inputs larger than L2 ({lb.lb_state_bytes(nx, ny, storage) / 1e9:.2f} GB per buffer)",
+                           "parallelism": f"replicas{world}"},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": traffic,
+                             "bytes_per_site": bytes_per_site, "peak_kind": peak_kind},
+                "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": "MLUPS",
+                        "h2d_bytes_per_step": 18 * 2 * sites * es / args.steps,
+                        "d2h_bytes_per_step": 7 * 8 / args.steps},
+                "gpu_launches": args.steps,
+                "clocks": clocks,
+                "status": lb.lb_strerror(status),
+                "impl": "gb300"}
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="couette4096_f32", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-steps", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

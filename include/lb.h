@@ -1,0 +1,181 @@
+/*
+ * lb.h -- C ABI of the GB300 (sm_103a) two-species soft-glassy lattice
+ * Boltzmann library (liblb.so).
+ *
+ * The library advances the two-species D2Q9 Shan-Chen model with competing
+ * interactions of Benzi, Sbragaglia, Succi, Bernaschi, Chibbaro
+ * (arXiv:0906.3611), Sec. II:
+ *   - lattice BGK with the forcing-shifted equilibrium, Eq. (be);
+ *   - pseudo-potential psi(rho) = rho0 (1 - exp(-rho/rho0)), Eq. (PSI);
+ *   - force F_s = F^a_s + F^r_s + F^X_s on the 25-speed lattice of Table I,
+ *     Eq. (FORCE): intra-species attraction on belt 1 (weights w), repulsion
+ *     on belts 1 and 2 (weights p), inter-species repulsion on belt 1 acting
+ *     on densities with coupling G_AB / rho0^2;
+ *   - streaming with periodic boundaries, or periodic in x with moving walls
+ *     in y (Couette; not in the paper, see LB_COUETTE).
+ *
+ * Conventions (all entry points):
+ *   - Every call returns LB_OK (0) or a negative error code; lb_strerror()
+ *     names it.  A NULL handle or an out-of-range argument gives LB_EINVAL and
+ *     leaves the handle unchanged.
+ *   - Population arrays exchanged with the host are FP64, layout
+ *     f[s][i][y][x] (s = 0 species A, 1 species B; x fastest), contiguous,
+ *     2*9*ny*nx doubles.  D2Q9 order i = 0..8:
+ *       (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1).
+ *     A state f(t) holds the populations after streaming and before the
+ *     collision of step t (the f_is(r, t) of Eq. (be)).
+ *   - Host buffers belong to the caller.  Device memory belongs to the handle
+ *     unless it was passed to lb_create_on().
+ *   - Work is enqueued on the CUDA stream given at creation (NULL = the
+ *     legacy default stream).  lb_step() is asynchronous; the calls that
+ *     return host data synchronise that stream.
+ *   - One handle must not be used from two host threads at once.
+ */
+#ifndef LB_H
+#define LB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LB_API __attribute__((visibility("default")))
+#else
+#define LB_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ---- */
+#define LB_OK 0
+#define LB_EINVAL (-1)   /* bad argument: sizes, tau <= 1/2, NULL handle, ... */
+#define LB_ENOMEM (-2)   /* device or host allocation failed                  */
+#define LB_ECUDA (-3)    /* a CUDA runtime call failed                        */
+#define LB_ETIMEOUT (-4) /* a bounded device wait gave up (status word)       */
+#define LB_EBUSY (-5)    /* resource in use (e.g. a slot table is full)       */
+#define LB_ENEGRHO (-6)  /* a species density <= 0 was met (status word)      */
+
+/* ---- boundary kinds ---- */
+#define LB_PERIODIC 0 /* periodic in x and y                                 */
+#define LB_COUETTE 1  /* periodic in x; halfway bounce-back walls at
+                         y = -1/2 (velocity (-U_wall, 0)) and y = ny - 1/2
+                         (velocity (+U_wall, 0)); Ladd's moving-wall term uses
+                         the species density of the fluid node at the start of
+                         the step; the force stencil sees the density field
+                         mirrored about each wall                           */
+
+/* ---- population storage in device memory (arithmetic: FP64 for LB_F64,
+ *      FP32 otherwise) ---- */
+#define LB_F64 0      /* double                                              */
+#define LB_F32 1      /* float                                               */
+#define LB_BF16_DEV 2 /* bfloat16 deviation f_i - w_i rho_ref,s (RN-even)    */
+#define LB_F16_DEV 3  /* IEEE half deviation f_i - w_i rho_ref,s (RN-even)   */
+
+/* ---- seeded initial densities (lb_init_random) ---- */
+#define LB_INIT_UNIFORM_NOISE 0 /* rho_A = init[0] + init[2] (2u1 - 1),
+                                   rho_B = init[1] + init[2] (2u2 - 1)      */
+#define LB_INIT_BERNOULLI 1     /* u0 < init[0] ? (rho_A, rho_B) = (init[1], init[2])
+                                                : (init[2], init[1]);
+                                   then rho_A += init[3] u1, rho_B += init[3] u2 */
+
+typedef struct lb_handle lb_handle; /* opaque, library-owned */
+
+typedef struct {
+  double tau[2];     /* relaxation times tau_A, tau_B (> 1/2), Eq. (be)          */
+  double rho0;       /* psi scale rho0 (> 0), Eq. (PSI)                          */
+  double G_AB;       /* inter-species coupling; the force uses G_AB/rho0^2,
+                        Eq. (FORCE) third line; positive = repulsion           */
+  double Ga[2];      /* G^a_s: intra-species belt-1 coupling, weights w_i      */
+  double Gr[2];      /* G^r_s: intra-species belts-1+2 coupling, weights p_i   */
+  int boundary;      /* LB_PERIODIC or LB_COUETTE                               */
+  double U_wall;     /* wall speed U for LB_COUETTE (lattice units)            */
+  int storage;       /* LB_F64, LB_F32, LB_BF16_DEV or LB_F16_DEV               */
+  double rho_ref[2]; /* reference densities of the *_DEV storages (ignored
+                        otherwise); exp(-rho_ref/rho0) is taken in FP64       */
+  int init_kind;     /* LB_INIT_UNIFORM_NOISE or LB_INIT_BERNOULLI              */
+  double init[6];    /* recipe parameters, see the LB_INIT_* kinds             */
+} lb_params;
+
+/* Bytes of one population buffer (2*9*ny*pitch elements of the storage type,
+ * pitch = nx rounded up to a multiple of 32).  0 for invalid arguments. */
+LB_API size_t lb_state_bytes(int nx, int ny, int storage);
+
+/* Create a lattice of nx x ny sites (nx, ny >= 5: the force stencil reaches
+ * two sites and a periodic wrap must not fold a site onto itself).  Allocates
+ * two population buffers (ping-pong) and small work areas on the current
+ * device.  `cuda_stream` is a cudaStream_t (NULL: legacy default stream).
+ * Populations are zero until lb_init_random() or lb_set_state(). */
+LB_API int lb_create(int nx, int ny, const lb_params *p, void *cuda_stream, lb_handle **out);
+
+/* As lb_create(), but the two population buffers are caller-owned device
+ * memory (e.g. PyTorch tensors) of at least lb_state_bytes() bytes each,
+ * 256-byte aligned; they must outlive the handle. */
+LB_API int lb_create_on(int nx, int ny, const lb_params *p, void *cuda_stream, void *buf0,
+                        void *buf1, size_t bytes_each, lb_handle **out);
+
+/* Fill the state with the seeded recipe p->init_kind / p->init: one
+ * Philox4x32-10 block (Salmon et al., SC'11) per site, counter = y*nx + x,
+ * key = seed; u_k = word_k * 2^-32; f_is = w_i rho_s (zero velocity).  The
+ * densities are formed in FP64 without fused multiply-adds, so they are
+ * bit-identical to a host evaluation of the same recipe.  Asynchronous. */
+LB_API int lb_init_random(lb_handle *h, uint64_t seed);
+
+/* Advance n >= 0 time steps of Eq. (be) on the device.  Asynchronous: the
+ * work is enqueued on the handle's stream (replays of a captured CUDA graph
+ * when n is large).  Errors met on the device are reported by lb_status(). */
+LB_API int lb_step(lb_handle *h, int64_t n);
+
+/* Observables of the current state f(t), FP64 on the device; synchronises.
+ * Any pointer may be NULL to skip that output.
+ *   rho[2*ny*nx]  species densities rho_s = sum_i f_is, layout [s][y][x];
+ *   u[2*ny*nx]    the common velocity of Sec. II,
+ *                 u = sum_s (1/tau_s) sum_i f_is c_i / sum_s rho_s/tau_s,
+ *                 layout [component][y][x];
+ *   stress[3]     { mean sigma_xy, wall_top, wall_bottom }:
+ *                 sigma_xy = -sum_s (1 - 1/(2 tau_s)) sum_i (f_is - f^eq_is) c_ix c_iy
+ *                 averaged over sites, f^eq the collision's shifted equilibrium;
+ *                 wall_top / wall_bottom = shear stress carried across the top /
+ *                 bottom wall by the next streaming (momentum exchange per unit
+ *                 wall length; 0 for LB_PERIODIC);
+ *   mass[4]       { sum rho_A, sum rho_B, P_x, P_y }, P = sum_s sum_i f_is c_i. */
+LB_API int lb_observables(lb_handle *h, double *rho, double *u, double *stress, double *mass);
+
+/* Copy the state out as FP64 (layout above); synchronises. */
+LB_API int lb_get_state(lb_handle *h, double *f);
+
+/* Replace the state with f (FP64, layout above), converted to the storage
+ * type with round-to-nearest-even; synchronises before returning. */
+LB_API int lb_set_state(lb_handle *h, const double *f);
+
+/* Native-format state exchange, no conversion: f[s][i][y][x] in the storage
+ * type (8, 4 or 2 bytes per element), 2*9*ny*nx elements, unpadded.
+ * lb_set_state_raw copies from host memory (pinned memory makes it a DMA at
+ * full link speed) and returns after enqueueing (asynchronous, like
+ * cudaMemcpyAsync: the host buffer must stay valid until the stream reaches
+ * the copy); lb_get_state_raw synchronises. */
+LB_API int lb_set_state_raw(lb_handle *h, const void *f);
+LB_API int lb_get_state_raw(lb_handle *h, void *f);
+
+/* Steps taken since the last lb_init_random / lb_set_state. */
+LB_API int64_t lb_time(const lb_handle *h);
+
+/* Read and clear the device status word; synchronises.  Returns LB_OK,
+ * LB_ENEGRHO (a density <= 0 was met: the velocity shift of that species was
+ * skipped there), or LB_ETIMEOUT. */
+LB_API int lb_status(lb_handle *h);
+
+/* Wait for all work enqueued by this handle. */
+LB_API int lb_sync(lb_handle *h);
+
+/* Free the handle and the device memory it owns. */
+LB_API void lb_destroy(lb_handle *h);
+
+/* Static text for an error code. */
+LB_API const char *lb_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LB_H */

@@ -1,0 +1,389 @@
+// lb_api.cu -- the C ABI of include/lb.h: handle life cycle, argument
+// validation, buffer ping-pong, CUDA-graph replay of the step loop and the
+// host transfers.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "lb.h"
+#include "lb_kernels.h"
+#include "lb_rows.h"
+
+using namespace lbk;
+
+struct lb_handle {
+  int nx = 0, ny = 0;
+  lb_params p{};
+  Geom g{};
+  PhysD ph{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  void* buf[2] = {nullptr, nullptr};
+  bool owns = false;
+  int cur = 0;            // buffer holding the current state f(t)
+  int64_t t = 0;          // steps since the last (re)initialisation
+  Status* d_status = nullptr;
+  double* d_partials = nullptr;
+  int partial_cap = 0;
+  double* d_out = nullptr;     // NOBS reduced observables
+  double* h_out = nullptr;     // pinned copy of d_out
+  double* d_stage = nullptr;   // lazily allocated FP64 staging (fields / state planes)
+  size_t stage_bytes = 0;
+  cudaStream_t cap_stream = nullptr;  // private stream used only for graph capture
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int graph_steps = 0;
+  int use_rows = 0;       // 1 if the row-streaming kernel serves this lattice
+};
+
+static const int kGraphSteps = 32;  // steps per captured graph (even: keeps buffer parity)
+
+static int ck(cudaError_t e) { return e == cudaSuccess ? LB_OK : LB_ECUDA; }
+
+extern "C" size_t lb_state_bytes(int nx, int ny, int storage) {
+  const size_t es = elem_size(storage);
+  if (nx < 5 || ny < 5 || es == 0) return 0;
+  const size_t pitch = ((size_t)nx + 31) / 32 * 32;
+  return 18 * (size_t)ny * pitch * es;
+}
+
+static int validate(int nx, int ny, const lb_params* p) {
+  if (!p || nx < 5 || ny < 5) return LB_EINVAL;
+  if ((long long)nx * ny > (1LL << 40)) return LB_EINVAL;
+  if (!(p->tau[0] > 0.5) || !(p->tau[1] > 0.5)) return LB_EINVAL;
+  if (!(p->rho0 > 0.0) || !isfinite(p->rho0)) return LB_EINVAL;
+  if (p->boundary != LB_PERIODIC && p->boundary != LB_COUETTE) return LB_EINVAL;
+  if (elem_size(p->storage) == 0) return LB_EINVAL;
+  if (p->init_kind != LB_INIT_UNIFORM_NOISE && p->init_kind != LB_INIT_BERNOULLI) return LB_EINVAL;
+  const double vals[] = {p->G_AB, p->Ga[0], p->Ga[1], p->Gr[0], p->Gr[1], p->U_wall,
+                         p->rho_ref[0], p->rho_ref[1], p->tau[0], p->tau[1]};
+  for (double v : vals)
+    if (!isfinite(v)) return LB_EINVAL;
+  return LB_OK;
+}
+
+static void fill_phys(lb_handle* h) {
+  const lb_params& p = h->p;
+  PhysD& d = h->ph;
+  const bool dev = (p.storage == LB_BF16_DEV || p.storage == LB_F16_DEV);
+  d.dev = dev ? 1 : 0;
+  for (int s = 0; s < 2; ++s) {
+    d.tau[s] = p.tau[s];
+    d.omega[s] = 1.0 / p.tau[s];
+    d.Ga[s] = p.Ga[s];
+    d.Gr[s] = p.Gr[s];
+    d.rho_ref[s] = dev ? p.rho_ref[s] : 0.0;
+    d.E[s] = exp(-d.rho_ref[s] / p.rho0);  // FP64 exponential of the reference shift
+  }
+  d.rho0 = p.rho0;
+  d.G_AB = p.G_AB;
+  d.U = (p.boundary == LB_COUETTE) ? p.U_wall : 0.0;
+}
+
+static int create_common(int nx, int ny, const lb_params* p, void* stream, void* b0, void* b1,
+                         size_t bytes_each, lb_handle** out) {
+  if (!out) return LB_EINVAL;
+  *out = nullptr;
+  int rc = validate(nx, ny, p);
+  if (rc) return rc;
+  lb_handle* h = new (std::nothrow) lb_handle();
+  if (!h) return LB_ENOMEM;
+  h->nx = nx;
+  h->ny = ny;
+  h->p = *p;
+  h->stream = (cudaStream_t)stream;
+  h->g.nx = nx;
+  h->g.ny = ny;
+  h->g.pitch = (nx + 31) / 32 * 32;
+  h->g.boundary = p->boundary;
+  h->g.plane = (long long)ny * h->g.pitch;
+  fill_phys(h);
+  cudaGetDevice(&h->device);
+  const size_t need = lb_state_bytes(nx, ny, p->storage);
+  if (b0 || b1) {
+    if (!b0 || !b1 || bytes_each < need || ((uintptr_t)b0 & 255) || ((uintptr_t)b1 & 255)) {
+      delete h;
+      return LB_EINVAL;
+    }
+    h->buf[0] = b0;
+    h->buf[1] = b1;
+    h->owns = false;
+  } else {
+    if (cudaMalloc(&h->buf[0], need) != cudaSuccess || cudaMalloc(&h->buf[1], need) != cudaSuccess) {
+      cudaGetLastError();
+      lb_destroy(h);
+      return LB_ENOMEM;
+    }
+    h->owns = true;
+  }
+  h->partial_cap = observe_blocks(h->g);
+  if (cudaMalloc(&h->d_status, sizeof(Status)) != cudaSuccess ||
+      cudaMalloc(&h->d_partials, (size_t)h->partial_cap * NOBS * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&h->d_out, NOBS * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost(&h->h_out, NOBS * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    lb_destroy(h);
+    return LB_ENOMEM;
+  }
+  if (cudaMemsetAsync(h->d_status, 0, sizeof(Status), h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->buf[0], 0, need, h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->buf[1], 0, need, h->stream) != cudaSuccess) {
+    lb_destroy(h);
+    return LB_ECUDA;
+  }
+  h->use_rows = rows_supported(h->g, p->storage) ? 1 : 0;
+  *out = h;
+  return LB_OK;
+}
+
+extern "C" int lb_create(int nx, int ny, const lb_params* p, void* stream, lb_handle** out) {
+  return create_common(nx, ny, p, stream, nullptr, nullptr, 0, out);
+}
+
+extern "C" int lb_create_on(int nx, int ny, const lb_params* p, void* stream, void* buf0,
+                            void* buf1, size_t bytes_each, lb_handle** out) {
+  if (!buf0 || !buf1) return LB_EINVAL;
+  return create_common(nx, ny, p, stream, buf0, buf1, bytes_each, out);
+}
+
+static void drop_graphs(lb_handle* h) {
+  for (int k = 0; k < 2; ++k)
+    if (h->graph[k]) {
+      cudaGraphExecDestroy(h->graph[k]);
+      h->graph[k] = nullptr;
+    }
+}
+
+extern "C" void lb_destroy(lb_handle* h) {
+  if (!h) return;
+  if (h->stream || h->d_status) cudaStreamSynchronize(h->stream);
+  drop_graphs(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->owns) {
+    cudaFree(h->buf[0]);
+    cudaFree(h->buf[1]);
+  }
+  cudaFree(h->d_status);
+  cudaFree(h->d_partials);
+  cudaFree(h->d_out);
+  cudaFree(h->d_stage);
+  if (h->h_out) cudaFreeHost(h->h_out);
+  cudaGetLastError();
+  delete h;
+}
+
+extern "C" int lb_init_random(lb_handle* h, uint64_t seed) {
+  if (!h) return LB_EINVAL;
+  int rc = ck(launch_init(h->p.storage, h->buf[0], h->g, h->ph, seed, h->p.init_kind, h->p.init,
+                          h->stream));
+  if (rc) return rc;
+  h->cur = 0;
+  h->t = 0;
+  return LB_OK;
+}
+
+// One step from buffer `from` into the other buffer.
+static cudaError_t step_once(lb_handle* h, int from, cudaStream_t st) {
+  const void* src = h->buf[from];
+  void* dst = h->buf[1 - from];
+  if (h->use_rows) return launch_step_rows(h->p.storage, src, dst, h->g, h->ph, h->d_status, st);
+  return launch_step_tile(h->p.storage, src, dst, h->g, h->ph, h->d_status, st);
+}
+
+static int ensure_graph(lb_handle* h, int from) {
+  if (h->graph[from]) return LB_OK;
+  if (!h->cap_stream) {
+    if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return LB_ECUDA;
+  }
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return LB_ECUDA;
+  int b = from;
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) {
+    e = step_once(h, b, h->cap_stream);
+    b = 1 - b;
+  }
+  cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
+  if (e != cudaSuccess || e2 != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return LB_ECUDA;
+  }
+  cudaError_t e3 = cudaGraphInstantiate(&h->graph[from], graph, 0);
+  cudaGraphDestroy(graph);
+  if (e3 != cudaSuccess) {
+    h->graph[from] = nullptr;
+    cudaGetLastError();
+    return LB_ECUDA;
+  }
+  h->graph_steps = kGraphSteps;
+  return LB_OK;
+}
+
+extern "C" int lb_step(lb_handle* h, int64_t n) {
+  if (!h || n < 0) return LB_EINVAL;
+  int64_t left = n;
+  if (left >= kGraphSteps) {
+    int rc = ensure_graph(h, h->cur);
+    if (rc) return rc;
+    while (left >= kGraphSteps) {
+      if (cudaGraphLaunch(h->graph[h->cur], h->stream) != cudaSuccess) return LB_ECUDA;
+      left -= kGraphSteps;  // even count: h->cur unchanged
+      h->t += kGraphSteps;
+    }
+  }
+  while (left > 0) {
+    if (step_once(h, h->cur, h->stream) != cudaSuccess) return LB_ECUDA;
+    h->cur = 1 - h->cur;
+    ++h->t;
+    --left;
+  }
+  return LB_OK;
+}
+
+static int ensure_stage(lb_handle* h, size_t bytes) {
+  if (h->stage_bytes >= bytes) return LB_OK;
+  if (h->d_stage) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->d_stage);
+    h->d_stage = nullptr;
+    h->stage_bytes = 0;
+  }
+  if (cudaMalloc(&h->d_stage, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return LB_ENOMEM;
+  }
+  h->stage_bytes = bytes;
+  return LB_OK;
+}
+
+extern "C" int lb_observables(lb_handle* h, double* rho, double* u, double* stress, double* mass) {
+  if (!h) return LB_EINVAL;
+  const size_t n = (size_t)h->nx * h->ny;
+  const void* src = h->buf[h->cur];
+  if (stress || mass) {
+    if (launch_observe(h->p.storage, src, h->g, h->ph, h->d_status, h->d_partials, h->partial_cap,
+                       h->d_out, h->stream) != cudaSuccess)
+      return LB_ECUDA;
+    if (cudaMemcpyAsync(h->h_out, h->d_out, NOBS * sizeof(double), cudaMemcpyDeviceToHost,
+                        h->stream) != cudaSuccess)
+      return LB_ECUDA;
+  }
+  if (rho || u) {
+    int rc = ensure_stage(h, 4 * n * sizeof(double));
+    if (rc) return rc;
+    if (launch_fields(h->p.storage, src, h->g, h->ph, h->d_stage, h->stream) != cudaSuccess)
+      return LB_ECUDA;
+    if (rho && cudaMemcpyAsync(rho, h->d_stage, 2 * n * sizeof(double), cudaMemcpyDeviceToHost,
+                               h->stream) != cudaSuccess)
+      return LB_ECUDA;
+    if (u && cudaMemcpyAsync(u, h->d_stage + 2 * n, 2 * n * sizeof(double),
+                             cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+      return LB_ECUDA;
+  }
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LB_ECUDA;
+  if (mass) {
+    mass[0] = h->h_out[0];
+    mass[1] = h->h_out[1];
+    mass[2] = h->h_out[2];
+    mass[3] = h->h_out[3];
+  }
+  if (stress) {
+    stress[0] = h->h_out[4] / (double)n;
+    stress[1] = (h->p.boundary == LB_COUETTE) ? h->h_out[5] / h->nx : 0.0;
+    stress[2] = (h->p.boundary == LB_COUETTE) ? h->h_out[6] / h->nx : 0.0;
+  }
+  return LB_OK;
+}
+
+extern "C" int lb_get_state(lb_handle* h, double* f) {
+  if (!h || !f) return LB_EINVAL;
+  const size_t n = (size_t)h->nx * h->ny;
+  int rc = ensure_stage(h, n * sizeof(double));
+  if (rc) return rc;
+  for (int q = 0; q < 18; ++q) {
+    if (launch_unpack_plane(h->p.storage, h->buf[h->cur], h->d_stage, h->g, h->ph, q, h->stream) !=
+        cudaSuccess)
+      return LB_ECUDA;
+    if (cudaMemcpyAsync(f + (size_t)q * n, h->d_stage, n * sizeof(double), cudaMemcpyDeviceToHost,
+                        h->stream) != cudaSuccess)
+      return LB_ECUDA;
+  }
+  return ck(cudaStreamSynchronize(h->stream));
+}
+
+extern "C" int lb_set_state(lb_handle* h, const double* f) {
+  if (!h || !f) return LB_EINVAL;
+  const size_t n = (size_t)h->nx * h->ny;
+  int rc = ensure_stage(h, n * sizeof(double));
+  if (rc) return rc;
+  for (int q = 0; q < 18; ++q) {
+    if (cudaMemcpyAsync(h->d_stage, f + (size_t)q * n, n * sizeof(double), cudaMemcpyHostToDevice,
+                        h->stream) != cudaSuccess)
+      return LB_ECUDA;
+    if (launch_pack_plane(h->p.storage, h->d_stage, h->buf[0], h->g, h->ph, q, h->stream) !=
+        cudaSuccess)
+      return LB_ECUDA;
+  }
+  h->cur = 0;
+  h->t = 0;
+  return ck(cudaStreamSynchronize(h->stream));
+}
+
+extern "C" int lb_set_state_raw(lb_handle* h, const void* f) {
+  if (!h || !f) return LB_EINVAL;
+  const size_t es = elem_size(h->p.storage);
+  if (cudaMemcpy2DAsync(h->buf[0], (size_t)h->g.pitch * es, f, (size_t)h->nx * es,
+                        (size_t)h->nx * es, (size_t)18 * h->ny, cudaMemcpyHostToDevice,
+                        h->stream) != cudaSuccess)
+    return LB_ECUDA;
+  h->cur = 0;
+  h->t = 0;
+  return LB_OK;
+}
+
+extern "C" int lb_get_state_raw(lb_handle* h, void* f) {
+  if (!h || !f) return LB_EINVAL;
+  const size_t es = elem_size(h->p.storage);
+  if (cudaMemcpy2DAsync(f, (size_t)h->nx * es, h->buf[h->cur], (size_t)h->g.pitch * es,
+                        (size_t)h->nx * es, (size_t)18 * h->ny, cudaMemcpyDeviceToHost,
+                        h->stream) != cudaSuccess)
+    return LB_ECUDA;
+  return ck(cudaStreamSynchronize(h->stream));
+}
+
+extern "C" int64_t lb_time(const lb_handle* h) { return h ? h->t : -1; }
+
+extern "C" int lb_status(lb_handle* h) {
+  if (!h) return LB_EINVAL;
+  Status s;
+  if (cudaMemcpyAsync(&s, h->d_status, sizeof(Status), cudaMemcpyDeviceToHost, h->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return LB_ECUDA;
+  if (cudaMemsetAsync(h->d_status, 0, sizeof(Status), h->stream) != cudaSuccess) return LB_ECUDA;
+  if (s.timeout) return LB_ETIMEOUT;
+  if (s.bad_rho) return LB_ENEGRHO;
+  return LB_OK;
+}
+
+extern "C" int lb_sync(lb_handle* h) {
+  if (!h) return LB_EINVAL;
+  return ck(cudaStreamSynchronize(h->stream));
+}
+
+extern "C" const char* lb_strerror(int code) {
+  switch (code) {
+    case LB_OK: return "ok";
+    case LB_EINVAL: return "invalid argument";
+    case LB_ENOMEM: return "out of memory";
+    case LB_ECUDA: return "CUDA runtime error";
+    case LB_ETIMEOUT: return "bounded device wait timed out";
+    case LB_EBUSY: return "resource busy";
+    case LB_ENEGRHO: return "non-positive species density met";
+  }
+  return "unknown error";
+}

@@ -1,0 +1,134 @@
+// lb_common.cuh -- shared device definitions of the GB300 lattice Boltzmann
+// library: D2Q9 speeds, the 25-speed forcing weights of Table I, storage
+// codecs and the per-launch argument blocks.
+//
+// Arithmetic is carried in "deviation" variables d_i = f_i - w_i rho_ref,s.
+// For plain FP64/FP32 storage rho_ref = 0 and d_i = f_i; for the 16-bit
+// storages the stored value is d_i itself.  Since sum_i w_i = 1 and
+// sum_i w_i c_i = 0, rho_s = rho_ref,s + sum_i d_i and the momentum is
+// sum_i d_i c_i, and the BGK update of Eq. (be) reads
+//   d*_i = d_i + (1/tau_s) (w_i (drho_s + rho_s q_i) - d_i),
+//   q_i  = c_i.v/cs2 + (c_ia c_ib - cs2 d_ab) v_a v_b / (2 cs2^2),  cs2 = 1/3,
+// which keeps the small deviations exact in FP32.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lb.h"
+
+namespace lbk {
+
+// ---- D2Q9 speeds (order of the public header) and equilibrium weights ----
+struct Q9 {
+  static __host__ __device__ constexpr int cx(int i) {
+    return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+  }
+  static __host__ __device__ constexpr int cy(int i) {
+    return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+  }
+  // opposite speed: 1<->3, 2<->4, 5<->7, 6<->8
+  static __host__ __device__ constexpr int opp(int i) {
+    return i == 0 ? 0 : (i <= 4 ? (i + 1) % 4 + 1 : (i - 3) % 4 + 5);
+  }
+};
+
+template <typename C>
+__host__ __device__ constexpr C wq(int i) {
+  return i == 0 ? C(4) / C(9) : (i <= 4 ? C(1) / C(9) : C(1) / C(36));
+}
+
+// ---- Table I weight groups by |c|^2 (1, 2, 4, 5, 8) ----
+// p: 4/63, 4/135, 1/180, 2/945, 1/15120 ; w (belt 1 only): 1/9, 1/36.
+__host__ __device__ constexpr int group_of(int dx, int dy) {
+  return (dx * dx + dy * dy == 1) ? 0
+         : (dx * dx + dy * dy == 2) ? 1
+         : (dx * dx + dy * dy == 4) ? 2
+         : (dx * dx + dy * dy == 5) ? 3
+                                    : 4;
+}
+
+// ---- storage codecs ----
+template <int STORAGE>
+struct Store;
+
+template <>
+struct Store<LB_F64> {
+  using T = double;
+  using C = double;
+  static __device__ __forceinline__ C ld(T v) { return v; }
+  static __device__ __forceinline__ T st(C v) { return v; }
+};
+template <>
+struct Store<LB_F32> {
+  using T = float;
+  using C = float;
+  static __device__ __forceinline__ C ld(T v) { return v; }
+  static __device__ __forceinline__ T st(C v) { return v; }
+};
+template <>
+struct Store<LB_BF16_DEV> {
+  using T = __nv_bfloat16;
+  using C = float;
+  static __device__ __forceinline__ C ld(T v) { return __bfloat162float(v); }
+  static __device__ __forceinline__ T st(C v) { return __float2bfloat16_rn(v); }
+};
+template <>
+struct Store<LB_F16_DEV> {
+  using T = __half;
+  using C = float;
+  static __device__ __forceinline__ C ld(T v) { return __half2float(v); }
+  static __device__ __forceinline__ T st(C v) { return __float2half_rn(v); }
+};
+
+// ---- per-launch physics constants (computed on the host in FP64) ----
+template <typename C>
+struct Phys {
+  C omega[2];    // 1/tau_s
+  C tau[2];      // tau_s
+  C rho0;        // psi scale
+  C inv_rho0;    // 1/rho0
+  C E[2];        // exp(-rho_ref,s/rho0), taken in FP64 (1 for plain storage)
+  C rho_ref[2];  // reference densities (0 for plain storage)
+  C Wpsi[2][5];  // psi-stencil weights Ga_s w + Gr_s p per |c|^2 group
+  C gw[2];       // (G_AB/rho0^2) w for |c|^2 = 1, 2 (inter-species term)
+  C Uwall;       // Couette wall speed
+};
+
+struct Geom {
+  int nx, ny;      // lattice
+  int pitch;       // elements per row in device memory (nx rounded up to 32)
+  int boundary;    // LB_PERIODIC / LB_COUETTE
+  long long plane; // elements per population plane = ny * pitch
+};
+
+// Device status word bits / counters.
+struct Status {
+  unsigned int bad_rho;  // count of (site, species) with rho_s <= 0
+  unsigned int timeout;  // nonzero if a bounded wait gave up
+  unsigned int pad[2];
+};
+
+__host__ __device__ __forceinline__ int wrapi(int a, int n) {
+  int r = a % n;
+  return r < 0 ? r + n : r;
+}
+
+// Row read by the force stencil: periodic, or mirrored about the walls at
+// y = -1/2 and y = ny - 1/2 (reflection with period 2 ny) for Couette.
+__host__ __device__ __forceinline__ int stencil_row(int y, int ny, int boundary) {
+  if (boundary != LB_COUETTE) return wrapi(y, ny);
+  int r = wrapi(y, 2 * ny);
+  return r >= ny ? 2 * ny - 1 - r : r;
+}
+
+template <typename C>
+__device__ __forceinline__ C exp_c(C x);
+template <>
+__device__ __forceinline__ double exp_c<double>(double x) { return exp(x); }
+template <>
+__device__ __forceinline__ float exp_c<float>(float x) { return expf(x); }
+
+}  // namespace lbk

@@ -1,0 +1,87 @@
+// lb_kernels.h -- host-side launchers of the device kernels (internal to
+// liblb.so; the public interface is include/lb.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lb_common.cuh"
+
+namespace lbk {
+
+// Physics constants in FP64, as prepared by the API layer from lb_params.
+struct PhysD {
+  double tau[2], omega[2], rho0, G_AB, Ga[2], Gr[2], U, rho_ref[2], E[2];
+  int dev;  // 1 for the deviation (16-bit) storages
+};
+
+// Number of FP64 observables accumulated per block by the observe kernels:
+// {sum rho_A, sum rho_B, P_x, P_y, sum sigma_xy, wall_top, wall_bottom, 0}.
+constexpr int NOBS = 8;
+
+size_t elem_size(int storage);
+
+// Generic fused step (tile kernel): pull-free "push" form, one launch per step.
+cudaError_t launch_step_tile(int storage, const void* src, void* dst, const Geom& g,
+                             const PhysD& ph, Status* status, cudaStream_t st);
+
+// Observables of a state: per-block partial sums into `partials` (capacity
+// `cap_blocks` blocks of NOBS doubles), then a single-block finalize into out[NOBS].
+cudaError_t launch_observe(int storage, const void* src, const Geom& g, const PhysD& ph,
+                           Status* status, double* partials, int cap_blocks, double* out,
+                           cudaStream_t st);
+int observe_blocks(const Geom& g);
+
+// Fields rho_A, rho_B, u_x, u_y (FP64, [4][ny][nx]) of a state.
+cudaError_t launch_fields(int storage, const void* src, const Geom& g, const PhysD& ph,
+                          double* fields, cudaStream_t st);
+
+// Seeded initial state (Philox4x32-10 per site).
+cudaError_t launch_init(int storage, void* dst, const Geom& g, const PhysD& ph, uint64_t seed,
+                        int kind, const double* init6, cudaStream_t st);
+
+// FP64 plane <-> storage plane conversion (plane index q = s*9 + i).
+cudaError_t launch_pack_plane(int storage, const double* in, void* state, const Geom& g,
+                              const PhysD& ph, int q, cudaStream_t st);
+cudaError_t launch_unpack_plane(int storage, const void* state, double* out, const Geom& g,
+                                const PhysD& ph, int q, cudaStream_t st);
+
+}  // namespace lbk
+
+namespace lbk {
+
+// Table I forcing weights per |c|^2 group (1, 2, 4, 5, 8): p for F^r on both
+// belts, w for F^a and F^X on belt 1.
+inline double table_p(int grp) {
+  const double p[5] = {4.0 / 63.0, 4.0 / 135.0, 1.0 / 180.0, 2.0 / 945.0, 1.0 / 15120.0};
+  return p[grp];
+}
+inline double table_w(int grp) {
+  const double w[5] = {1.0 / 9.0, 1.0 / 36.0, 0.0, 0.0, 0.0};
+  return w[grp];
+}
+
+// Per-launch constants in the kernel's arithmetic type.  The psi-stencil
+// weight of a speed of group k for species s is Ga_s w_k + Gr_s p_k
+// (Eq. (FORCE), first two lines folded), the inter-species weight is
+// (G_AB/rho0^2) w_k (third line).
+template <typename C>
+inline Phys<C> make_phys(const PhysD& d) {
+  Phys<C> p;
+  const double g = d.G_AB / (d.rho0 * d.rho0);
+  for (int s = 0; s < 2; ++s) {
+    p.omega[s] = (C)d.omega[s];
+    p.tau[s] = (C)d.tau[s];
+    p.E[s] = (C)d.E[s];
+    p.rho_ref[s] = (C)d.rho_ref[s];
+    for (int k = 0; k < 5; ++k) p.Wpsi[s][k] = (C)(d.Ga[s] * table_w(k) + d.Gr[s] * table_p(k));
+  }
+  p.rho0 = (C)d.rho0;
+  p.inv_rho0 = (C)(1.0 / d.rho0);
+  p.gw[0] = (C)(g * table_w(0));
+  p.gw[1] = (C)(g * table_w(1));
+  p.Uwall = (C)d.U;
+  return p;
+}
+
+}  // namespace lbk

@@ -1,0 +1,77 @@
+// lb_site.cuh -- per-site arithmetic of one time step (Sec. II of the paper),
+// shared by every step kernel and by the observables kernel.
+#pragma once
+
+#include "lb_common.cuh"
+
+namespace lbk {
+
+// Moments of one site from its deviations d[s][i]:
+//   j_s = sum_i d_is c_i  (= sum_i f_is c_i, since sum_i w_i c_i = 0).
+template <typename C>
+__device__ __forceinline__ void momenta(const C (&d)[2][9], C (&jx)[2], C (&jy)[2]) {
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    jx[s] = (d[s][1] - d[s][3]) + (d[s][5] - d[s][6]) + (d[s][8] - d[s][7]);
+    jy[s] = (d[s][2] - d[s][4]) + (d[s][5] - d[s][8]) + (d[s][6] - d[s][7]);
+  }
+}
+
+// Common velocity u = sum_s j_s/tau_s / sum_s rho_s/tau_s and the shifted
+// velocities v_s = u + tau_s F_s / rho_s of the equilibrium in Eq. (be).
+// A species with rho_s <= 0 gets no shift; `bad` counts those.
+template <typename C>
+__device__ __forceinline__ void shifted_velocities(const Phys<C>& ph, const C (&rho)[2],
+                                                   const C (&jx)[2], const C (&jy)[2],
+                                                   const C (&Fx)[2], const C (&Fy)[2],
+                                                   C (&vx)[2], C (&vy)[2], int& bad) {
+  const C den = rho[0] * ph.omega[0] + rho[1] * ph.omega[1];
+  const C ux = (jx[0] * ph.omega[0] + jx[1] * ph.omega[1]) / den;
+  const C uy = (jy[0] * ph.omega[0] + jy[1] * ph.omega[1]) / den;
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    vx[s] = ux;
+    vy[s] = uy;
+    if (rho[s] > C(0)) {
+      const C k = ph.tau[s] / rho[s];
+      vx[s] += k * Fx[s];
+      vy[s] += k * Fy[s];
+    } else {
+      ++bad;
+    }
+  }
+}
+
+// Equilibrium deviation deq_i = w_i (drho + rho q_i) of the truncated
+// Maxwellian of Sec. II at velocity v (cs2 = 1/3).
+template <typename C>
+__device__ __forceinline__ C eq_dev(int i, C drho, C rho, C vx, C vy, C usq15) {
+  const C cu = C(Q9::cx(i)) * vx + C(Q9::cy(i)) * vy;
+  const C q = C(3) * cu + C(4.5) * cu * cu - usq15;
+  return wq<C>(i) * (drho + rho * q);
+}
+
+// BGK relaxation of Eq. (be) in deviation form, in place: d_i -> d*_i.
+template <typename C>
+__device__ __forceinline__ void bgk(const Phys<C>& ph, C (&d)[2][9], const C (&drho)[2],
+                                    const C (&rho)[2], const C (&vx)[2], const C (&vy)[2]) {
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const C usq15 = C(1.5) * (vx[s] * vx[s] + vy[s] * vy[s]);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const C deq = eq_dev<C>(i, drho[s], rho[s], vx[s], vy[s], usq15);
+      d[s][i] = d[s][i] + ph.omega[s] * (deq - d[s][i]);
+    }
+  }
+}
+
+// Ladd's moving-wall term for a link i leaving the fluid through a wall of
+// velocity (Uw, 0): the population returns reversed, reduced by
+// 2 w_i rho_s (c_i . U_w) / cs2.
+template <typename C>
+__device__ __forceinline__ C wall_term(int i, C rho_s, C Uw) {
+  return C(6) * wq<C>(i) * rho_s * C(Q9::cx(i)) * Uw;
+}
+
+}  // namespace lbk

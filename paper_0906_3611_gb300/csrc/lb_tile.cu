@@ -1,0 +1,321 @@
+// lb_tile.cu -- generic fused step kernel (2-D tiles) and the observables
+// kernels.
+//
+// One CTA owns a 32 x 8 tile of sites.  It first computes rho_s and
+// psi_s = rho0 (1 - exp(-rho_s/rho0)) (Eq. (PSI)) on the tile plus a halo of
+// two sites into shared memory (the force stencil of Table I reaches |c| = 2
+// in each direction), then each thread takes one site: moments, the force of
+// Eq. (FORCE) from the shared tile, the shifted-velocity BGK collision of
+// Eq. (be), and the push of f*_i to r + c_i (Ladd bounce-back at Couette
+// walls).  This kernel handles every storage type and lattice size; the
+// row-streaming kernel (lb_rows.cu) is the bandwidth-tuned path.
+#include "lb_kernels.h"
+#include "lb_site.cuh"
+
+namespace lbk {
+
+constexpr int TTX = 32, TTY = 8;
+constexpr int TEX = TTX + 4, TEY = TTY + 4;
+constexpr int TTHREADS = TTX * TTY;
+
+template <int STORAGE, bool OBSERVE>
+__global__ void __launch_bounds__(TTHREADS)
+    k_tile(const typename Store<STORAGE>::T* __restrict__ src,
+           typename Store<STORAGE>::T* __restrict__ dst, Geom g,
+           Phys<typename Store<STORAGE>::C> ph, Status* status, double* __restrict__ partials) {
+  using S = Store<STORAGE>;
+  using T = typename S::T;
+  using C = typename S::C;
+  __shared__ C s_rho[2][TEY][TEX];
+  __shared__ C s_psi[2][TEY][TEX];
+
+  const int x0 = blockIdx.x * TTX, y0 = blockIdx.y * TTY;
+  const int tid = threadIdx.x;
+
+  // -- densities and pseudo-potentials on the tile + halo 2 --
+  for (int e = tid; e < TEX * TEY; e += TTHREADS) {
+    const int ex = e % TEX, ey = e / TEX;
+    const int gx = wrapi(x0 + ex - 2, g.nx);
+    const int gy = stencil_row(y0 + ey - 2, g.ny, g.boundary);
+    const T* p = src + (long long)gy * g.pitch + gx;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      C dr = C(0);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) dr += S::ld(p[(long long)(s * 9 + i) * g.plane]);
+      s_rho[s][ey][ex] = ph.rho_ref[s] + dr;
+      s_psi[s][ey][ex] = ph.rho0 * (C(1) - ph.E[s] * exp_c<C>(-dr * ph.inv_rho0));
+    }
+  }
+  __syncthreads();
+
+  const int tx = tid % TTX, ty = tid / TTX;
+  const int x = x0 + tx, y = y0 + ty;
+  const bool active = (x < g.nx) && (y < g.ny);
+  double acc[NOBS];
+#pragma unroll
+  for (int k = 0; k < NOBS; ++k) acc[k] = 0.0;
+  int bad = 0;
+
+  if (active) {
+    C d[2][9];
+    const T* p = src + (long long)y * g.pitch + x;
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int i = 0; i < 9; ++i) d[s][i] = S::ld(p[(long long)(s * 9 + i) * g.plane]);
+
+    C drho[2], rho[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      C a = C(0);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) a += d[s][i];
+      drho[s] = a;
+      rho[s] = ph.rho_ref[s] + a;
+    }
+
+    // -- force, Eq. (FORCE): psi stencil over both belts, rho stencil on belt 1 --
+    C Fx[2], Fy[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      C sx = C(0), sy = C(0), xx = C(0), xy = C(0);
+#pragma unroll
+      for (int dy = -2; dy <= 2; ++dy)
+#pragma unroll
+        for (int dx = -2; dx <= 2; ++dx) {
+          if (dx == 0 && dy == 0) continue;
+          const int k = group_of(dx, dy);
+          const C ps = s_psi[s][ty + 2 + dy][tx + 2 + dx];
+          sx += ph.Wpsi[s][k] * ps * C(dx);
+          sy += ph.Wpsi[s][k] * ps * C(dy);
+          if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) {
+            const C ro = s_rho[1 - s][ty + 2 + dy][tx + 2 + dx];
+            xx += ph.gw[k] * ro * C(dx);
+            xy += ph.gw[k] * ro * C(dy);
+          }
+        }
+      const C pc = s_psi[s][ty + 2][tx + 2];
+      Fx[s] = -pc * sx - rho[s] * xx;
+      Fy[s] = -pc * sy - rho[s] * xy;
+    }
+
+    C jx[2], jy[2];
+    momenta<C>(d, jx, jy);
+    C vx[2], vy[2];
+    shifted_velocities<C>(ph, rho, jx, jy, Fx, Fy, vx, vy, bad);
+
+    if (OBSERVE) {
+      acc[0] = (double)rho[0];
+      acc[1] = (double)rho[1];
+      acc[2] = (double)jx[0] + (double)jx[1];
+      acc[3] = (double)jy[0] + (double)jy[1];
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const C usq15 = C(1.5) * (vx[s] * vx[s] + vy[s] * vy[s]);
+        double neq_xy = 0.0;
+#pragma unroll
+        for (int i = 5; i < 9; ++i) {
+          const C deq = eq_dev<C>(i, drho[s], rho[s], vx[s], vy[s], usq15);
+          neq_xy += (double)(d[s][i] - deq) * (double)(Q9::cx(i) * Q9::cy(i));
+        }
+        acc[4] -= (1.0 - 0.5 * (double)ph.omega[s]) * neq_xy;
+        if (g.boundary == LB_COUETTE && (y == 0 || y == g.ny - 1)) {
+#pragma unroll
+          for (int i = 1; i < 9; ++i) {
+            const int yd = y + Q9::cy(i);
+            if (yd >= 0 && yd < g.ny) continue;
+            const C deq = eq_dev<C>(i, drho[s], rho[s], vx[s], vy[s], usq15);
+            const C dstar = d[s][i] + ph.omega[s] * (deq - d[s][i]);
+            const double fp = (double)(wq<C>(i) * ph.rho_ref[s] + dstar);
+            const C Uw = (yd >= g.ny) ? ph.Uwall : -ph.Uwall;
+            const double back = fp - (double)wall_term<C>(i, rho[s], Uw);
+            const double push = (double)Q9::cx(i) * (fp + back);
+            if (yd >= g.ny)
+              acc[5] -= push;
+            else
+              acc[6] += push;
+          }
+        }
+      }
+    } else {
+      bgk<C>(ph, d, drho, rho, vx, vy);
+      // -- push f*_i to r + c_i; links through a wall come back reversed --
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          int yd = y + Q9::cy(i);
+          if (g.boundary == LB_COUETTE && (yd < 0 || yd >= g.ny)) {
+            const C Uw = (yd >= g.ny) ? ph.Uwall : -ph.Uwall;
+            const C val = d[s][i] - wall_term<C>(i, rho[s], Uw);
+            dst[(long long)(s * 9 + Q9::opp(i)) * g.plane + (long long)y * g.pitch + x] = S::st(val);
+          } else {
+            yd = wrapi(yd, g.ny);
+            const int xd = wrapi(x + Q9::cx(i), g.nx);
+            dst[(long long)(s * 9 + i) * g.plane + (long long)yd * g.pitch + xd] = S::st(d[s][i]);
+          }
+        }
+    }
+  }
+  if (bad) atomicAdd(&status->bad_rho, (unsigned)bad);
+
+  if (OBSERVE) {
+    // deterministic tree reduction of the block's sums
+    __shared__ double red[NOBS][TTHREADS];
+#pragma unroll
+    for (int k = 0; k < NOBS; ++k) red[k][tid] = acc[k];
+    __syncthreads();
+    for (int stride = TTHREADS / 2; stride > 0; stride >>= 1) {
+      if (tid < stride) {
+#pragma unroll
+        for (int k = 0; k < NOBS; ++k) red[k][tid] += red[k][tid + stride];
+      }
+      __syncthreads();
+    }
+    if (tid < NOBS) {
+      const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+      partials[b * NOBS + tid] = red[tid][0];
+    }
+  }
+}
+
+// Single-block finalize: sum the per-block partials in a fixed order.
+__global__ void __launch_bounds__(256) k_finalize(const double* __restrict__ partials, int nblocks,
+                                                  double* __restrict__ out) {
+  __shared__ double red[NOBS][256];
+  const int tid = threadIdx.x;
+  double a[NOBS];
+#pragma unroll
+  for (int k = 0; k < NOBS; ++k) a[k] = 0.0;
+  for (int b = tid; b < nblocks; b += 256)
+#pragma unroll
+    for (int k = 0; k < NOBS; ++k) a[k] += partials[(long long)b * NOBS + k];
+#pragma unroll
+  for (int k = 0; k < NOBS; ++k) red[k][tid] = a[k];
+  __syncthreads();
+  for (int stride = 128; stride > 0; stride >>= 1) {
+    if (tid < stride) {
+#pragma unroll
+      for (int k = 0; k < NOBS; ++k) red[k][tid] += red[k][tid + stride];
+    }
+    __syncthreads();
+  }
+  if (tid < NOBS) out[tid] = red[tid][0];
+}
+
+// rho_A, rho_B and the common velocity u of Sec. II, FP64 fields [4][ny][nx].
+template <int STORAGE>
+__global__ void __launch_bounds__(256)
+    k_fields(const typename Store<STORAGE>::T* __restrict__ src, Geom g,
+             Phys<typename Store<STORAGE>::C> ph, double* __restrict__ out) {
+  using S = Store<STORAGE>;
+  using T = typename S::T;
+  using C = typename S::C;
+  const long long n = (long long)g.nx * g.ny;
+  for (long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x; site < n;
+       site += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(site / g.nx), x = (int)(site % g.nx);
+    const T* p = src + (long long)y * g.pitch + x;
+    C d[2][9];
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int i = 0; i < 9; ++i) d[s][i] = S::ld(p[(long long)(s * 9 + i) * g.plane]);
+    C rho[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      C a = C(0);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) a += d[s][i];
+      rho[s] = ph.rho_ref[s] + a;
+    }
+    C jx[2], jy[2];
+    momenta<C>(d, jx, jy);
+    const C den = rho[0] * ph.omega[0] + rho[1] * ph.omega[1];
+    out[site] = (double)rho[0];
+    out[n + site] = (double)rho[1];
+    out[2 * n + site] = (double)((jx[0] * ph.omega[0] + jx[1] * ph.omega[1]) / den);
+    out[3 * n + site] = (double)((jy[0] * ph.omega[0] + jy[1] * ph.omega[1]) / den);
+  }
+}
+
+// ---- launchers ----
+
+static dim3 tile_grid(const Geom& g) { return dim3((g.nx + TTX - 1) / TTX, (g.ny + TTY - 1) / TTY); }
+
+int observe_blocks(const Geom& g) {
+  const dim3 gr = tile_grid(g);
+  return (int)(gr.x * gr.y);
+}
+
+template <int STORAGE>
+static cudaError_t step_tile_t(const void* src, void* dst, const Geom& g, const PhysD& pd,
+                               Status* status, cudaStream_t st) {
+  using S = Store<STORAGE>;
+  k_tile<STORAGE, false><<<tile_grid(g), TTHREADS, 0, st>>>(
+      (const typename S::T*)src, (typename S::T*)dst, g, make_phys<typename S::C>(pd), status,
+      nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_tile(int storage, const void* src, void* dst, const Geom& g,
+                             const PhysD& ph, Status* status, cudaStream_t st) {
+  switch (storage) {
+    case LB_F64: return step_tile_t<LB_F64>(src, dst, g, ph, status, st);
+    case LB_F32: return step_tile_t<LB_F32>(src, dst, g, ph, status, st);
+    case LB_BF16_DEV: return step_tile_t<LB_BF16_DEV>(src, dst, g, ph, status, st);
+    case LB_F16_DEV: return step_tile_t<LB_F16_DEV>(src, dst, g, ph, status, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int STORAGE>
+static cudaError_t observe_t(const void* src, const Geom& g, const PhysD& pd, Status* status,
+                             double* partials, cudaStream_t st) {
+  using S = Store<STORAGE>;
+  k_tile<STORAGE, true><<<tile_grid(g), TTHREADS, 0, st>>>(
+      (const typename S::T*)src, nullptr, g, make_phys<typename S::C>(pd), status, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_observe(int storage, const void* src, const Geom& g, const PhysD& ph,
+                           Status* status, double* partials, int cap_blocks, double* out,
+                           cudaStream_t st) {
+  const int nb = observe_blocks(g);
+  if (nb > cap_blocks) return cudaErrorInvalidValue;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (storage) {
+    case LB_F64: e = observe_t<LB_F64>(src, g, ph, status, partials, st); break;
+    case LB_F32: e = observe_t<LB_F32>(src, g, ph, status, partials, st); break;
+    case LB_BF16_DEV: e = observe_t<LB_BF16_DEV>(src, g, ph, status, partials, st); break;
+    case LB_F16_DEV: e = observe_t<LB_F16_DEV>(src, g, ph, status, partials, st); break;
+  }
+  if (e != cudaSuccess) return e;
+  k_finalize<<<1, 256, 0, st>>>(partials, nb, out);
+  return cudaGetLastError();
+}
+
+template <int STORAGE>
+static cudaError_t fields_t(const void* src, const Geom& g, const PhysD& pd, double* out,
+                            cudaStream_t st) {
+  using S = Store<STORAGE>;
+  const long long n = (long long)g.nx * g.ny;
+  const int blocks = (int)((n + 255) / 256 < 152 * 16 ? (n + 255) / 256 : 152 * 16);
+  k_fields<STORAGE><<<blocks, 256, 0, st>>>((const typename S::T*)src, g,
+                                            make_phys<typename S::C>(pd), out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fields(int storage, const void* src, const Geom& g, const PhysD& ph,
+                          double* fields, cudaStream_t st) {
+  switch (storage) {
+    case LB_F64: return fields_t<LB_F64>(src, g, ph, fields, st);
+    case LB_F32: return fields_t<LB_F32>(src, g, ph, fields, st);
+    case LB_BF16_DEV: return fields_t<LB_BF16_DEV>(src, g, ph, fields, st);
+    case LB_F16_DEV: return fields_t<LB_F16_DEV>(src, g, ph, fields, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace lbk

@@ -1,0 +1,258 @@
+"""Thin ctypes binding of liblb.so (include/lb.h), names as in the C ABI.
+
+Argument marshalling only: every step of the lattice Boltzmann update runs in
+the library's CUDA kernels.  PyTorch provides device memory (the two
+population buffers, via ``lb_create_on``) and CUDA streams.  If the library
+is missing, importing this module raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblb.so")
+
+LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_ETIMEOUT, LB_EBUSY, LB_ENEGRHO = 0, -1, -2, -3, -4, -5, -6
+LB_PERIODIC, LB_COUETTE = 0, 1
+LB_F64, LB_F32, LB_BF16_DEV, LB_F16_DEV = 0, 1, 2, 3
+LB_INIT_UNIFORM_NOISE, LB_INIT_BERNOULLI = 0, 1
+ELEM_BYTES = {LB_F64: 8, LB_F32: 4, LB_BF16_DEV: 2, LB_F16_DEV: 2}
+
+# every entry point declared in include/lb.h
+EXPORTED = ["lb_state_bytes", "lb_create", "lb_create_on", "lb_init_random", "lb_step",
+            "lb_observables", "lb_get_state", "lb_set_state", "lb_set_state_raw",
+            "lb_get_state_raw", "lb_time", "lb_status", "lb_sync", "lb_destroy", "lb_strerror"]
+
+
+class lb_params(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double * 2), ("rho0", ctypes.c_double), ("G_AB", ctypes.c_double),
+                ("Ga", ctypes.c_double * 2), ("Gr", ctypes.c_double * 2), ("boundary", ctypes.c_int),
+                ("U_wall", ctypes.c_double), ("storage", ctypes.c_int),
+                ("rho_ref", ctypes.c_double * 2), ("init_kind", ctypes.c_int),
+                ("init", ctypes.c_double * 6)]
+
+
+class LBError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {lb_strerror(code)} ({code})")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp = ctypes.c_void_p
+    dp = ctypes.POINTER(ctypes.c_double)
+    hp = ctypes.POINTER(vp)
+    pp = ctypes.POINTER(lb_params)
+    sig = {
+        "lb_state_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "lb_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, pp, vp, hp]),
+        "lb_create_on": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, pp, vp, vp, vp, ctypes.c_size_t, hp]),
+        "lb_init_random": (ctypes.c_int, [vp, ctypes.c_uint64]),
+        "lb_step": (ctypes.c_int, [vp, ctypes.c_int64]),
+        "lb_observables": (ctypes.c_int, [vp, dp, dp, dp, dp]),
+        "lb_get_state": (ctypes.c_int, [vp, dp]),
+        "lb_set_state": (ctypes.c_int, [vp, dp]),
+        "lb_set_state_raw": (ctypes.c_int, [vp, vp]),
+        "lb_get_state_raw": (ctypes.c_int, [vp, vp]),
+        "lb_time": (ctypes.c_int64, [vp]),
+        "lb_status": (ctypes.c_int, [vp]),
+        "lb_sync": (ctypes.c_int, [vp]),
+        "lb_destroy": (None, [vp]),
+        "lb_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def _dp(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _check(rc: int, what: str):
+    if rc != LB_OK:
+        raise LBError(rc, what)
+
+
+def make_params(tau=(1.0, 1.0), rho0=0.7, G_AB=0.405, Ga=(-9.0, -9.0), Gr=(8.1, 8.1),
+                boundary=LB_PERIODIC, U_wall=0.0, storage=LB_F32, rho_ref=(1.0, 1.0),
+                init_kind=LB_INIT_UNIFORM_NOISE, init=(1.0, 1.0, 0.05)) -> lb_params:
+    p = lb_params()
+    p.tau[:] = list(tau)
+    p.rho0 = rho0
+    p.G_AB = G_AB
+    p.Ga[:] = list(Ga)
+    p.Gr[:] = list(Gr)
+    p.boundary = boundary
+    p.U_wall = U_wall
+    p.storage = storage
+    p.rho_ref[:] = list(rho_ref)
+    p.init_kind = init_kind
+    iv = list(init) + [0.0] * (6 - len(init))
+    p.init[:] = iv
+    return p
+
+
+# ---- the C ABI, one Python function per entry point ----
+
+def lb_state_bytes(nx: int, ny: int, storage: int) -> int:
+    return int(_lib.lb_state_bytes(nx, ny, storage))
+
+
+def lb_create(nx: int, ny: int, params: lb_params, stream: int | None = None) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.lb_create(nx, ny, ctypes.byref(params), ctypes.c_void_p(stream or 0),
+                          ctypes.byref(h)), "lb_create")
+    return h.value
+
+
+def lb_create_on(nx: int, ny: int, params: lb_params, stream: int | None, buf0: int, buf1: int,
+                 bytes_each: int) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.lb_create_on(nx, ny, ctypes.byref(params), ctypes.c_void_p(stream or 0),
+                             ctypes.c_void_p(buf0), ctypes.c_void_p(buf1), bytes_each,
+                             ctypes.byref(h)), "lb_create_on")
+    return h.value
+
+
+def lb_init_random(h: int, seed: int) -> None:
+    _check(_lib.lb_init_random(h, ctypes.c_uint64(seed)), "lb_init_random")
+
+
+def lb_step(h: int, n: int) -> None:
+    _check(_lib.lb_step(h, n), "lb_step")
+
+
+def lb_observables(h: int, rho=None, u=None, stress=None, mass=None) -> None:
+    _check(_lib.lb_observables(h, _dp(rho), _dp(u), _dp(stress), _dp(mass)), "lb_observables")
+
+
+def lb_get_state(h: int, f: np.ndarray) -> None:
+    _check(_lib.lb_get_state(h, _dp(f)), "lb_get_state")
+
+
+def lb_set_state(h: int, f: np.ndarray) -> None:
+    _check(_lib.lb_set_state(h, _dp(np.ascontiguousarray(f, dtype=np.float64))), "lb_set_state")
+
+
+def lb_set_state_raw(h: int, ptr: int) -> None:
+    _check(_lib.lb_set_state_raw(h, ctypes.c_void_p(ptr)), "lb_set_state_raw")
+
+
+def lb_get_state_raw(h: int, ptr: int) -> None:
+    _check(_lib.lb_get_state_raw(h, ctypes.c_void_p(ptr)), "lb_get_state_raw")
+
+
+def lb_time(h: int) -> int:
+    return int(_lib.lb_time(h))
+
+
+def lb_status(h: int) -> int:
+    return int(_lib.lb_status(h))
+
+
+def lb_sync(h: int) -> None:
+    _check(_lib.lb_sync(h), "lb_sync")
+
+
+def lb_destroy(h: int) -> None:
+    _lib.lb_destroy(h)
+
+
+def lb_strerror(code: int) -> str:
+    return _lib.lb_strerror(code).decode()
+
+
+class Lattice:
+    """One lattice on the current CUDA device, populations in torch-owned memory.
+
+    ``params`` is an ``lb_params`` (see ``make_params``).  ``stream`` is a
+    ``torch.cuda.Stream`` (default: a new one).  Device memory for the two
+    population buffers comes from PyTorch and is passed to ``lb_create_on``.
+    """
+
+    def __init__(self, nx: int, ny: int, params: lb_params, stream=None, torch_buffers: bool = True):
+        import torch
+
+        self.nx, self.ny, self.params = nx, ny, params
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        sptr = self.stream.cuda_stream
+        self.bytes_each = lb_state_bytes(nx, ny, params.storage)
+        if self.bytes_each == 0:
+            raise LBError(LB_EINVAL, "lb_state_bytes")
+        self._bufs = None
+        if torch_buffers:
+            self._bufs = [torch.empty(self.bytes_each, dtype=torch.uint8, device="cuda") for _ in range(2)]
+            torch.cuda.current_stream().synchronize()
+            self.h = lb_create_on(nx, ny, params, sptr, self._bufs[0].data_ptr(),
+                                  self._bufs[1].data_ptr(), self.bytes_each)
+        else:
+            self.h = lb_create(nx, ny, params, sptr)
+
+    def init_random(self, seed: int):
+        lb_init_random(self.h, seed)
+        return self
+
+    def step(self, n: int = 1):
+        lb_step(self.h, n)
+        return self
+
+    def observables(self, fields: bool = False) -> dict:
+        stress = np.zeros(3)
+        mass = np.zeros(4)
+        rho = u = None
+        if fields:
+            rho = np.zeros((2, self.ny, self.nx))
+            u = np.zeros((2, self.ny, self.nx))
+        lb_observables(self.h, rho, u, stress, mass)
+        out = {"stress": stress, "mass": mass}
+        if fields:
+            out["rho"] = rho
+            out["u"] = u
+        return out
+
+    def get_state(self) -> np.ndarray:
+        f = np.empty((2, 9, self.ny, self.nx))
+        lb_get_state(self.h, f)
+        return f
+
+    def set_state(self, f: np.ndarray):
+        lb_set_state(self.h, f)
+        return self
+
+    @property
+    def time(self) -> int:
+        return lb_time(self.h)
+
+    def status(self) -> int:
+        return lb_status(self.h)
+
+    def sync(self):
+        lb_sync(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lb_destroy(self.h)
+            self.h = None
+        self._bufs = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
