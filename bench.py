@@ -34,6 +34,7 @@ WORKLOADS = {
     # name: (nx, ny, boundary, U, storage)
     "couette4096_f32": (4096, 4096, 1, 0.02, 1),
     "emulsion1024_f32": (1024, 1024, 0, 0.0, 1),
+    "couette2048_f32": (2048, 2048, 1, 0.02, 1),
     "couette4096_bf16dev": (4096, 4096, 1, 0.02, 2),
     "couette4096_f16dev": (4096, 4096, 1, 0.02, 3),
 }
