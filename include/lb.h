@@ -55,6 +55,7 @@ extern "C" {
 #define LB_ETIMEOUT (-4) /* a bounded device wait gave up (status word)       */
 #define LB_EBUSY (-5)    /* resource in use (e.g. a slot table is full)       */
 #define LB_ENEGRHO (-6)  /* a species density <= 0 was met (status word)      */
+#define LB_ETOOBIG (-7)  /* lattice larger than a fixed-size static work area */
 
 /* ---- boundary kinds ---- */
 #define LB_PERIODIC 0 /* periodic in x and y                                 */
@@ -170,6 +171,30 @@ LB_API int lb_sync(lb_handle *h);
 
 /* Free the handle and the device memory it owns. */
 LB_API void lb_destroy(lb_handle *h);
+
+/* Observables of a caller-owned state without allocating any memory.  The
+ * paper has no counterpart: this is an interface for callers that cannot call
+ * cudaMalloc -- e.g. an application whose own pool allocator owns all device
+ * memory, or a running stream pipeline that must not take the device-wide
+ * synchronisation cudaMalloc/cudaFree can cause.  It computes the same
+ * quantities as lb_observables(stress, mass) but needs no handle.
+ *   f      device pointer to a population buffer in the library's device
+ *          layout: 18 planes [s*9+i] of ny rows of `pitch` (>= nx) elements of
+ *          the storage type p->storage (for a handle's buffer, pitch = nx
+ *          rounded up to a multiple of 32);
+ *   out    device pointer to 8 doubles, written on `cuda_stream`:
+ *          { sum rho_A, sum rho_B, P_x, P_y, mean sigma_xy, wall_top,
+ *            wall_bottom, count of (site, species) with rho_s <= 0 }.
+ * The partial sums live in a fixed static device array of 4 MiB + 64 B that
+ * every GPU loading the library holds until exit; it serves lattices of up to
+ * 65536 tiles of 32 x 8 sites (e.g. 4096 x 4096), larger ones get
+ * LB_ETOOBIG.  The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array: calls whose work
+ * overlaps on the GPU race and must be serialised by the caller.
+ * Asynchronous: returns after enqueueing; allocates nothing. */
+LB_API int lb_observables_noalloc(const void *f, int nx, int ny, int pitch, const lb_params *p,
+                                  void *cuda_stream, double *out);
 
 /* Static text for an error code. */
 LB_API const char *lb_strerror(int code);

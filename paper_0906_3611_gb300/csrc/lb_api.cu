@@ -384,6 +384,7 @@ extern "C" const char* lb_strerror(int code) {
     case LB_ETIMEOUT: return "bounded device wait timed out";
     case LB_EBUSY: return "resource busy";
     case LB_ENEGRHO: return "non-positive species density met";
+    case LB_ETOOBIG: return "lattice too large for the fixed static work area";
   }
   return "unknown error";
 }

@@ -16,6 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblb.so")
 
 LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_ETIMEOUT, LB_EBUSY, LB_ENEGRHO = 0, -1, -2, -3, -4, -5, -6
+LB_ETOOBIG = -7
 LB_PERIODIC, LB_COUETTE = 0, 1
 LB_F64, LB_F32, LB_BF16_DEV, LB_F16_DEV = 0, 1, 2, 3
 LB_INIT_UNIFORM_NOISE, LB_INIT_BERNOULLI = 0, 1
@@ -24,7 +25,8 @@ ELEM_BYTES = {LB_F64: 8, LB_F32: 4, LB_BF16_DEV: 2, LB_F16_DEV: 2}
 # every entry point declared in include/lb.h
 EXPORTED = ["lb_state_bytes", "lb_create", "lb_create_on", "lb_init_random", "lb_step",
             "lb_observables", "lb_get_state", "lb_set_state", "lb_set_state_raw",
-            "lb_get_state_raw", "lb_time", "lb_status", "lb_sync", "lb_destroy", "lb_strerror"]
+            "lb_get_state_raw", "lb_time", "lb_status", "lb_sync", "lb_destroy", "lb_strerror",
+            "lb_observables_noalloc"]
 
 
 class lb_params(ctypes.Structure):
@@ -66,6 +68,8 @@ def _load():
         "lb_sync": (ctypes.c_int, [vp]),
         "lb_destroy": (None, [vp]),
         "lb_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "lb_observables_noalloc": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, pp,
+                                                  vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -172,6 +176,15 @@ def lb_sync(h: int) -> None:
 
 def lb_destroy(h: int) -> None:
     _lib.lb_destroy(h)
+
+
+def lb_observables_noalloc(f_ptr: int, nx: int, ny: int, pitch: int, params: lb_params,
+                           stream: int | None, out_ptr: int) -> None:
+    """Observables of a device population buffer into 8 device doubles, with no
+    allocation (for callers that cannot call cudaMalloc; see include/lb.h)."""
+    _check(_lib.lb_observables_noalloc(ctypes.c_void_p(f_ptr), nx, ny, pitch, ctypes.byref(params),
+                                       ctypes.c_void_p(stream or 0), ctypes.c_void_p(out_ptr)),
+           "lb_observables_noalloc")
 
 
 def lb_strerror(code: int) -> str:
