@@ -93,6 +93,7 @@ struct Phys {
   C E[2];        // exp(-rho_ref,s/rho0), taken in FP64 (1 for plain storage)
   C rho_ref[2];  // reference densities (0 for plain storage)
   C Wpsi[2][5];  // psi-stencil weights Ga_s w + Gr_s p per |c|^2 group
+  C W2psi[2][3]; // twice the weights of groups |c|^2 = 4, 5, 8 (the x-offset 2 terms)
   C gw[2];       // (G_AB/rho0^2) w for |c|^2 = 1, 2 (inter-species term)
   C Uwall;       // Couette wall speed
 };
@@ -124,11 +125,22 @@ __host__ __device__ __forceinline__ int stencil_row(int y, int ny, int boundary)
   return r >= ny ? 2 * ny - 1 - r : r;
 }
 
+// Exponential and division in the kernel's arithmetic type.  FP64 uses the
+// correctly rounded library forms; FP32 uses the hardware approximations
+// (__expf: a few ulp on the range of -rho/rho0 met here; __fdividef: 2 ulp),
+// far inside the 1e-5 tolerance of the FP32 path.
 template <typename C>
 __device__ __forceinline__ C exp_c(C x);
 template <>
 __device__ __forceinline__ double exp_c<double>(double x) { return exp(x); }
 template <>
-__device__ __forceinline__ float exp_c<float>(float x) { return expf(x); }
+__device__ __forceinline__ float exp_c<float>(float x) { return __expf(x); }
+
+template <typename C>
+__device__ __forceinline__ C div_c(C a, C b);
+template <>
+__device__ __forceinline__ double div_c<double>(double a, double b) { return a / b; }
+template <>
+__device__ __forceinline__ float div_c<float>(float a, float b) { return __fdividef(a, b); }
 
 }  // namespace lbk

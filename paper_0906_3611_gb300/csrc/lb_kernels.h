@@ -75,6 +75,8 @@ inline Phys<C> make_phys(const PhysD& d) {
     p.E[s] = (C)d.E[s];
     p.rho_ref[s] = (C)d.rho_ref[s];
     for (int k = 0; k < 5; ++k) p.Wpsi[s][k] = (C)(d.Ga[s] * table_w(k) + d.Gr[s] * table_p(k));
+    for (int k = 0; k < 3; ++k)
+      p.W2psi[s][k] = (C)(2.0 * (d.Ga[s] * table_w(k + 2) + d.Gr[s] * table_p(k + 2)));
   }
   p.rho0 = (C)d.rho0;
   p.inv_rho0 = (C)(1.0 / d.rho0);

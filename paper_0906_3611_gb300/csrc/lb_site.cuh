@@ -26,14 +26,14 @@ __device__ __forceinline__ void shifted_velocities(const Phys<C>& ph, const C (&
                                                    const C (&Fx)[2], const C (&Fy)[2],
                                                    C (&vx)[2], C (&vy)[2], int& bad) {
   const C den = rho[0] * ph.omega[0] + rho[1] * ph.omega[1];
-  const C ux = (jx[0] * ph.omega[0] + jx[1] * ph.omega[1]) / den;
-  const C uy = (jy[0] * ph.omega[0] + jy[1] * ph.omega[1]) / den;
+  const C ux = div_c<C>(jx[0] * ph.omega[0] + jx[1] * ph.omega[1], den);
+  const C uy = div_c<C>(jy[0] * ph.omega[0] + jy[1] * ph.omega[1], den);
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     vx[s] = ux;
     vy[s] = uy;
     if (rho[s] > C(0)) {
-      const C k = ph.tau[s] / rho[s];
+      const C k = div_c<C>(ph.tau[s], rho[s]);
       vx[s] += k * Fx[s];
       vy[s] += k * Fy[s];
     } else {

@@ -72,7 +72,10 @@ def test_seeded_init_is_bit_identical(lb, kind, init, shape):
     assert np.array_equal(f, ref)
 
 
-SHAPES = [(64, 64), (67, 45), (5, 5), (37, 5), (5, 23), (131, 17)]
+# tile kernel: nx below one 128-column strip (or odd); row-streaming kernel: the rest,
+# with ragged last strips (264 = 2*128 + 8) and 1..3-row ranges per CTA
+SHAPES = [(64, 64), (67, 45), (5, 5), (37, 5), (5, 23), (131, 17),
+          (256, 64), (264, 37), (132, 19), (390, 11), (1024, 8)]
 
 
 @pytest.mark.parametrize("boundary,U", [(0, 0.0), (1, 0.03)])
@@ -191,8 +194,8 @@ def test_observables_parity_fp64(lb, boundary, U):
     assert np.allclose(ob["u"], ref["u"], rtol=1e-11, atol=1e-15)
 
 
-def test_graph_replay_equals_eager_steps(lb):
-    nx, ny = 96, 80
+@pytest.mark.parametrize("nx,ny", [(96, 80), (256, 80)])
+def test_graph_replay_equals_eager_steps(lb, nx, ny):
     p = _params(lb, CFG, lb.LB_F32, kind=1, init=(0.7, 1.2, 0.1, 0.02))
     a = lb.Lattice(nx, ny, p).init_random(3)
     b = lb.Lattice(nx, ny, p).init_random(3)
@@ -256,3 +259,32 @@ def test_full_size_sampled_sites_fp32_couette(lb):
     for (ys, xs) in sites:
         ref = _patch_reference(rho0f, ys, xs, ny, nx, CFG, 1, U, np.float32)
         assert _rel_err(got[:, :, ys, xs].astype(np.float64), ref) <= 1e-5, (ys, xs)
+
+
+@pytest.mark.parametrize("boundary,U", [(0, 0.0), (1, 0.03)])
+@pytest.mark.parametrize("shape", [(520, 41), (136, 9), (4096, 6)])
+def test_fp32_one_step_rows_kernel(lb, shape, boundary, U):
+    """FP32 storage on the row-streaming kernel: one step within 1e-5 of FP64."""
+    nx, ny = shape
+    f = inputs.populations(nx, ny, seed=nx + ny, base=W9, rel_amp=0.05, species_scale=(0.9, 1.1))
+    f = f.astype(np.float32).astype(np.float64)
+    lat = lb.Lattice(nx, ny, _params(lb, ASYM, lb.LB_F32, boundary, U))
+    g = lat.set_state(f).step(1).get_state()
+    assert lat.status() == lb.LB_OK
+    lat.close()
+    ref, _ = oracle.step(f, _oracle_p(ASYM, boundary, U), 1)
+    assert _rel_err(g, ref) <= 1e-5
+
+
+def test_tile_and_rows_kernels_agree(lb, monkeypatch):
+    """The two step kernels of the library, FP64, 40 steps of a droplet run."""
+    nx, ny = 264, 40
+    p = _params(lb, CFG, lb.LB_F64, boundary=1, U=0.02, kind=1, init=(0.7, 1.2, 0.1, 0.02))
+    out = {}
+    for kern in ("tile", "rows"):
+        monkeypatch.setenv("LB_STEP_KERNEL", kern)
+        lat = lb.Lattice(nx, ny, p).init_random(9).step(40)
+        out[kern] = lat.get_state()
+        assert lat.status() == lb.LB_OK
+        lat.close()
+    assert _scaled_err(out["rows"], out["tile"]) <= 1e-11
