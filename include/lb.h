@@ -98,8 +98,9 @@ typedef struct {
   double init[6];    /* recipe parameters, see the LB_INIT_* kinds             */
 } lb_params;
 
-/* Bytes of one population buffer (2*9*ny*pitch elements of the storage type,
- * pitch = nx rounded up to a multiple of 32).  0 for invalid arguments. */
+/* Bytes of one population buffer: 9 direction planes of ny rows of pitch
+ * sites (pitch = nx rounded up to a multiple of 32), two species per site,
+ * in the storage type.  0 for invalid arguments. */
 LB_API size_t lb_state_bytes(int nx, int ny, int storage);
 
 /* Create a lattice of nx x ny sites (nx, ny >= 5: the force stencil reaches
@@ -149,8 +150,9 @@ LB_API int lb_get_state(lb_handle *h, double *f);
  * type with round-to-nearest-even; synchronises before returning. */
 LB_API int lb_set_state(lb_handle *h, const double *f);
 
-/* Native-format state exchange, no conversion: f[s][i][y][x] in the storage
- * type (8, 4 or 2 bytes per element), 2*9*ny*nx elements, unpadded.
+/* Native-format state exchange, no conversion: the device's own element order
+ * without row padding, f[i][y][x][s] (direction, row, column, species) in the
+ * storage type (8, 4 or 2 bytes per element), 9*ny*nx*2 elements.
  * lb_set_state_raw copies from host memory (pinned memory makes it a DMA at
  * full link speed) and returns after enqueueing (asynchronous, like
  * cudaMemcpyAsync: the host buffer must stay valid until the stream reaches
@@ -179,9 +181,9 @@ LB_API void lb_destroy(lb_handle *h);
  * synchronisation cudaMalloc/cudaFree can cause.  It computes the same
  * quantities as lb_observables(stress, mass) but needs no handle.
  *   f      device pointer to a population buffer in the library's device
- *          layout: 18 planes [s*9+i] of ny rows of `pitch` (>= nx) elements of
- *          the storage type p->storage (for a handle's buffer, pitch = nx
- *          rounded up to a multiple of 32);
+ *          layout: element (s, i, y, x) of the storage type p->storage at
+ *          index 2*((i*ny + y)*pitch + x) + s, pitch >= nx sites per row (for
+ *          a handle's buffer, pitch = nx rounded up to a multiple of 32);
  *   out    device pointer to 8 doubles, written on `cuda_stream`:
  *          { sum rho_A, sum rho_B, P_x, P_y, mean sigma_xy, wall_top,
  *            wall_bottom, count of (site, species) with rho_s <= 0 }.

@@ -346,8 +346,8 @@ extern "C" int lb_set_state(lb_handle* h, const double* f) {
 extern "C" int lb_set_state_raw(lb_handle* h, const void* f) {
   if (!h || !f) return LB_EINVAL;
   const size_t es = elem_size(h->p.storage);
-  if (cudaMemcpy2DAsync(h->buf[0], (size_t)h->g.pitch * es, f, (size_t)h->nx * es,
-                        (size_t)h->nx * es, (size_t)18 * h->ny, cudaMemcpyHostToDevice,
+  if (cudaMemcpy2DAsync(h->buf[0], (size_t)2 * h->g.pitch * es, f, (size_t)2 * h->nx * es,
+                        (size_t)2 * h->nx * es, (size_t)9 * h->ny, cudaMemcpyHostToDevice,
                         h->stream) != cudaSuccess)
     return LB_ECUDA;
   h->cur = 0;
@@ -358,8 +358,8 @@ extern "C" int lb_set_state_raw(lb_handle* h, const void* f) {
 extern "C" int lb_get_state_raw(lb_handle* h, void* f) {
   if (!h || !f) return LB_EINVAL;
   const size_t es = elem_size(h->p.storage);
-  if (cudaMemcpy2DAsync(f, (size_t)h->nx * es, h->buf[h->cur], (size_t)h->g.pitch * es,
-                        (size_t)h->nx * es, (size_t)18 * h->ny, cudaMemcpyDeviceToHost,
+  if (cudaMemcpy2DAsync(f, (size_t)2 * h->nx * es, h->buf[h->cur], (size_t)2 * h->g.pitch * es,
+                        (size_t)2 * h->nx * es, (size_t)9 * h->ny, cudaMemcpyDeviceToHost,
                         h->stream) != cudaSuccess)
     return LB_ECUDA;
   return ck(cudaStreamSynchronize(h->stream));

@@ -98,12 +98,21 @@ struct Phys {
   C Uwall;       // Couette wall speed
 };
 
+// Device layout of a population buffer: one plane per D2Q9 direction i, rows
+// of `pitch` sites, and the two species of a site side by side, so that
+// element (s, i, y, x) sits at 2 * (i * plane + y * pitch + x) + s.  Each
+// direction is a structure-of-arrays plane (coalesced along x), and one
+// 2-wide access reads both species of a site.
 struct Geom {
   int nx, ny;      // lattice
-  int pitch;       // elements per row in device memory (nx rounded up to 32)
+  int pitch;       // sites per row in device memory (nx rounded up to 32)
   int boundary;    // LB_PERIODIC / LB_COUETTE
-  long long plane; // elements per population plane = ny * pitch
+  long long plane; // sites per direction plane = ny * pitch
 };
+
+__host__ __device__ __forceinline__ long long lidx(const Geom& g, int s, int i, int y, int x) {
+  return 2 * ((long long)i * g.plane + (long long)y * g.pitch + x) + s;
+}
 
 // Device status word bits / counters.
 struct Status {

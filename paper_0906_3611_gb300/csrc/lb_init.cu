@@ -83,14 +83,13 @@ __global__ void __launch_bounds__(256)
       rB = __dadd_rn(rB, __dmul_rn(a.init[3], u2));
     }
     const int y = (int)(site / g.nx), x = (int)(site % g.nx);
-    const long long o = (long long)y * g.pitch + x;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const double wi = wq<double>(i);
       const double fA = __dsub_rn(__dmul_rn(wi, rA), __dmul_rn(wi, a.rho_ref[0]));
       const double fB = __dsub_rn(__dmul_rn(wi, rB), __dmul_rn(wi, a.rho_ref[1]));
-      dst[(long long)i * g.plane + o] = from_double<STORAGE>(fA);
-      dst[(long long)(9 + i) * g.plane + o] = from_double<STORAGE>(fB);
+      dst[lidx(g, 0, i, y, x)] = from_double<STORAGE>(fA);
+      dst[lidx(g, 1, i, y, x)] = from_double<STORAGE>(fB);
     }
   }
 }
@@ -98,24 +97,24 @@ __global__ void __launch_bounds__(256)
 template <int STORAGE>
 __global__ void __launch_bounds__(256)
     k_pack(const double* __restrict__ in, typename Store<STORAGE>::T* __restrict__ state, Geom g,
-           double base) {
+           int s, int i, double base) {
   const long long n = (long long)g.nx * g.ny;
   for (long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x; site < n;
        site += (long long)gridDim.x * blockDim.x) {
     const int y = (int)(site / g.nx), x = (int)(site % g.nx);
-    state[(long long)y * g.pitch + x] = from_double<STORAGE>(__dsub_rn(in[site], base));
+    state[lidx(g, s, i, y, x)] = from_double<STORAGE>(__dsub_rn(in[site], base));
   }
 }
 
 template <int STORAGE>
 __global__ void __launch_bounds__(256)
     k_unpack(const typename Store<STORAGE>::T* __restrict__ state, double* __restrict__ out, Geom g,
-             double base) {
+             int s, int i, double base) {
   const long long n = (long long)g.nx * g.ny;
   for (long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x; site < n;
        site += (long long)gridDim.x * blockDim.x) {
     const int y = (int)(site / g.nx), x = (int)(site % g.nx);
-    out[site] = __dadd_rn(base, to_double<STORAGE>(state[(long long)y * g.pitch + x]));
+    out[site] = __dadd_rn(base, to_double<STORAGE>(state[lidx(g, s, i, y, x)]));
   }
 }
 
@@ -159,16 +158,18 @@ static double plane_base(const PhysD& ph, int q) {
 template <int STORAGE>
 static cudaError_t pack_t(const double* in, void* state, const Geom& g, const PhysD& ph, int q,
                           cudaStream_t st) {
-  auto* p = (typename Store<STORAGE>::T*)state + (long long)q * g.plane;
-  k_pack<STORAGE><<<grid_for((long long)g.nx * g.ny), 256, 0, st>>>(in, p, g, plane_base(ph, q));
+  auto* p = (typename Store<STORAGE>::T*)state;
+  k_pack<STORAGE><<<grid_for((long long)g.nx * g.ny), 256, 0, st>>>(in, p, g, q / 9, q % 9,
+                                                                    plane_base(ph, q));
   return cudaGetLastError();
 }
 
 template <int STORAGE>
 static cudaError_t unpack_t(const void* state, double* out, const Geom& g, const PhysD& ph, int q,
                             cudaStream_t st) {
-  auto* p = (const typename Store<STORAGE>::T*)state + (long long)q * g.plane;
-  k_unpack<STORAGE><<<grid_for((long long)g.nx * g.ny), 256, 0, st>>>(p, out, g, plane_base(ph, q));
+  auto* p = (const typename Store<STORAGE>::T*)state;
+  k_unpack<STORAGE><<<grid_for((long long)g.nx * g.ny), 256, 0, st>>>(p, out, g, q / 9, q % 9,
+                                                                      plane_base(ph, q));
   return cudaGetLastError();
 }
 

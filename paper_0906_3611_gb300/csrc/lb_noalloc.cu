@@ -57,12 +57,11 @@ __global__ void __launch_bounds__(NA_THREADS)
     const int ex = e % NA_EX, ey = e / NA_EX;
     const int gx = wrapi(x0 + ex - 2, g.nx);
     const int gy = stencil_row(y0 + ey - 2, g.ny, g.boundary);
-    const T* p = src + (long long)gy * g.pitch + gx;
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       C dr = C(0);
 #pragma unroll
-      for (int i = 0; i < 9; ++i) dr += S::ld(p[(long long)(s * 9 + i) * g.plane]);
+      for (int i = 0; i < 9; ++i) dr += S::ld(src[lidx(g, s, i, gy, gx)]);
       s_rho[s][ey][ex] = ph.rho_ref[s] + dr;
       s_psi[s][ey][ex] = ph.rho0 * (C(1) - ph.E[s] * exp_c<C>(-dr * ph.inv_rho0));
     }
@@ -77,11 +76,10 @@ __global__ void __launch_bounds__(NA_THREADS)
   int bad = 0;
   if (x < g.nx && y < g.ny) {
     C d[2][9];
-    const T* p = src + (long long)y * g.pitch + x;
 #pragma unroll
     for (int s = 0; s < 2; ++s)
 #pragma unroll
-      for (int i = 0; i < 9; ++i) d[s][i] = S::ld(p[(long long)(s * 9 + i) * g.plane]);
+      for (int i = 0; i < 9; ++i) d[s][i] = S::ld(src[lidx(g, s, i, y, x)]);
     C drho[2], rho[2];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {

@@ -1,0 +1,87 @@
+// lb_pair.cuh -- species-pair arithmetic for the row-streaming kernel.
+//
+// Both species of a site go through the same arithmetic, so a value is held
+// as a pair (species A in .x, species B in .y).  In FP32 the pair operations
+// map to the packed two-wide FP32 instructions (one add, multiply or fused
+// multiply-add on both species at once); in FP64 they are two scalar
+// operations.  The pair storage codecs read and write the two species of a
+// site, which sit side by side in device memory, with one access.
+#pragma once
+
+#include "lb_common.cuh"
+
+namespace lbk {
+
+template <typename C>
+struct PairOf;
+template <>
+struct PairOf<float> {
+  using P = float2;
+};
+template <>
+struct PairOf<double> {
+  using P = double2;
+};
+
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b as one packed fused multiply-add (b * -1 is exact)
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+__device__ __forceinline__ float2 pbc(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 pmk(float a, float b) { return make_float2(a, b); }
+
+__device__ __forceinline__ double2 padd(double2 a, double2 b) {
+  return make_double2(a.x + b.x, a.y + b.y);
+}
+__device__ __forceinline__ double2 pmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x, a.y * b.y);
+}
+__device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ double2 psub(double2 a, double2 b) {
+  return make_double2(a.x - b.x, a.y - b.y);
+}
+__device__ __forceinline__ double2 pbc(double v) { return make_double2(v, v); }
+__device__ __forceinline__ double2 pmk(double a, double b) { return make_double2(a, b); }
+
+template <typename P>
+__device__ __forceinline__ P pswap(P a) {
+  P r;
+  r.x = a.y;
+  r.y = a.x;
+  return r;
+}
+
+// ---- pair storage codecs: the two species of one (direction, site) ----
+template <int STORAGE>
+struct PairStore;
+template <>
+struct PairStore<LB_F64> {
+  using T2 = double2;
+  static __device__ __forceinline__ double2 ld(T2 v) { return v; }
+  static __device__ __forceinline__ T2 st(double2 v) { return v; }
+};
+template <>
+struct PairStore<LB_F32> {
+  using T2 = float2;
+  static __device__ __forceinline__ float2 ld(T2 v) { return v; }
+  static __device__ __forceinline__ T2 st(float2 v) { return v; }
+};
+template <>
+struct PairStore<LB_BF16_DEV> {
+  using T2 = __nv_bfloat162;
+  static __device__ __forceinline__ float2 ld(T2 v) { return __bfloat1622float2(v); }
+  static __device__ __forceinline__ T2 st(float2 v) { return __float22bfloat162_rn(v); }
+};
+template <>
+struct PairStore<LB_F16_DEV> {
+  using T2 = __half2;
+  static __device__ __forceinline__ float2 ld(T2 v) { return __half22float2(v); }
+  static __device__ __forceinline__ T2 st(float2 v) { return __float22half2_rn(v); }
+};
+
+}  // namespace lbk

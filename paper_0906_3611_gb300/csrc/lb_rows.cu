@@ -1,31 +1,36 @@
 // lb_rows.cu -- row-streaming fused step kernel (the bandwidth path).
 //
 // Each CTA owns a strip of RX = 128 columns and a contiguous range of rows,
-// and walks down the rows once.  Row r of the state f(t) (all 18 population
-// planes, columns x0-SOFF .. x0+RX+SOFF-1, periodic in x) is staged in shared
-// memory by bulk asynchronous copies (the TMA engine, cp.async.bulk) into a
-// ring of NSLOT slots guarded by mbarriers, NSLOT-2 rows ahead of use.
+// and walks down the rows once.  Row r of the state f(t) (the 9 direction
+// planes, both species of each site side by side, columns x0-SOFF ..
+// x0+RX+SOFF-1, periodic in x) is staged in shared memory by bulk
+// asynchronous copies (the TMA engine, cp.async.bulk) into a ring of NSLOT
+// slots guarded by mbarriers, NSLOT-4 rows ahead of use.
 //
-// For every staged row the CTA forms rho_s and psi_s (Eq. (PSI)) on the
-// strip plus two halo columns, then each thread (one per column) adds the
-// row's contribution to the 5 x 5 force stencil of its column (Eq. (FORCE),
-// Table I) into register accumulators of the five rows it touches.  The
-// stencil is separable per row: with D1 = psi(x+1)-psi(x-1),
-// D2 = psi(x+2)-psi(x-2), P1 = psi(x+1)+psi(x-1), P2 = psi(x+2)+psi(x-2),
+// One thread serves one column and carries both species as a pair (packed
+// two-wide FP32 arithmetic).  For every staged row it forms rho and
+// psi = rho0 (1 - exp(-rho/rho0)) (Eq. (PSI)) of its column; the row is
+// shared through shared memory (double-buffered, one barrier per row), and
+// the thread adds the row's contribution to the 5 x 5 force stencil of its
+// column (Eq. (FORCE), Table I) into register accumulators of the five rows
+// the row touches.  The stencil is separable per row: with
+// D1 = psi(x+1)-psi(x-1), D2 = psi(x+2)-psi(x-2), P1 = psi(x+1)+psi(x-1),
+// P2 = psi(x+2)+psi(x-2),
 //   sum_c W(c) psi(r+c) c_x = sum_dy [W(1,dy) D1 + 2 W(2,dy) D2](y+dy)
 //   sum_c W(c) psi(r+c) c_y = [H1(y+1) - H1(y-1)] + 2 [H2(y+2) - H2(y-2)],
 //   H1 = W(0,1) psi + W(1,1) P1 + W(2,1) P2,  H2 = W(0,2) psi + W(1,2) P1 + W(2,2) P2,
-// and likewise (belt 1 only) for the inter-species density term.  When the
-// row two below has all its contributions, that row's sites collide (the
-// shifted BGK of Eq. (be)) with their populations re-read from the staged
-// slot, and push f*_i to r + c_i in global memory (Ladd bounce-back at Couette
-// walls).  Every population is read from DRAM once and written once; the
-// halos (2 columns, 2+2 rows per range) are served by L2 or recomputed.
+// and likewise on belt 1 for the inter-species density term (the other
+// species' density: the pair swapped).  When the row two below has all its
+// contributions, its sites collide (the shifted BGK of Eq. (be)) with their
+// populations re-read from the staged slot, and push f*_i to r + c_i in
+// global memory (Ladd bounce-back at Couette walls).  Every population is
+// read from DRAM once and written once; the halos (2 columns, 2+2 rows per
+// range) are served by L2 or recomputed.
 //
-// Warps 0-3 compute one column each; warp 4 issues the bulk copies and forms
-// rho/psi of the four halo columns.  Every mbarrier wait is bounded: on
-// timeout the kernel sets the status word, drains its own copies (bounded)
-// and leaves.
+// Warps 0-3 compute; warp 4 issues the bulk copies and forms rho/psi of the
+// four halo columns.  Every mbarrier wait is bounded: on timeout the kernel
+// sets the status word, drains its own copies (bounded) and leaves.
+#include "lb_pair.cuh"
 #include "lb_rows.h"
 #include "lb_site.cuh"
 
@@ -34,23 +39,25 @@ namespace lbk {
 constexpr int RX = 128;            // interior columns per strip
 constexpr int RTHREADS = RX + 32;  // 4 compute warps + 1 copy/halo warp
 
+// SOFF: halo sites staged on each side (>= 2, a 16-byte multiple of pairs);
+// NSLOT: ring depth; MINB: CTAs per SM the register budget is sized for.
 template <int STORAGE>
 struct RowsCfg;
 template <>
 struct RowsCfg<LB_F64> {
-  static constexpr int SOFF = 2, NSLOT = 5, MINB = 2;  // 16 B = 2 doubles
+  static constexpr int SOFF = 2, NSLOT = 5, MINB = 2;  // 16-byte pairs
 };
 template <>
 struct RowsCfg<LB_F32> {
-  static constexpr int SOFF = 4, NSLOT = 7, MINB = 3;  // 16 B = 4 floats
+  static constexpr int SOFF = 2, NSLOT = 7, MINB = 3;  // 8-byte pairs
 };
 template <>
 struct RowsCfg<LB_BF16_DEV> {
-  static constexpr int SOFF = 8, NSLOT = 9, MINB = 3;  // 16 B = 8 halves
+  static constexpr int SOFF = 4, NSLOT = 9, MINB = 3;  // 4-byte pairs
 };
 template <>
 struct RowsCfg<LB_F16_DEV> {
-  static constexpr int SOFF = 8, NSLOT = 9, MINB = 3;
+  static constexpr int SOFF = 4, NSLOT = 9, MINB = 3;
 };
 
 template <int STORAGE>
@@ -60,9 +67,10 @@ constexpr int stage_width() {
 
 template <int STORAGE>
 constexpr size_t rows_smem_bytes() {
-  using S = Store<STORAGE>;
-  return (size_t)RowsCfg<STORAGE>::NSLOT * 18 * stage_width<STORAGE>() * sizeof(typename S::T) +
-         2 * 4 * (RX + 4) * sizeof(typename S::C) + 16 * RowsCfg<STORAGE>::NSLOT;
+  using T2 = typename PairStore<STORAGE>::T2;
+  using P = typename PairOf<typename Store<STORAGE>::C>::P;
+  return (size_t)RowsCfg<STORAGE>::NSLOT * 9 * stage_width<STORAGE>() * sizeof(T2) +
+         2 * 2 * (RX + 4) * sizeof(P) + 8 * RowsCfg<STORAGE>::NSLOT;
 }
 
 // ---- mbarrier / bulk-copy primitives (PTX) ----
@@ -109,23 +117,23 @@ __device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, u
       : "memory");
 }
 
-// Stage row r (all 18 planes, columns x0-SOFF .. x0+RX+SOFF-1 wrapped in x)
-// into `slot`.  Called by a whole warp: lane 0 posts the byte count of the row
-// on the slot's mbarrier, then lanes 0..17 each copy one plane (one bulk copy,
-// or two where the window crosses the periodic seam).
+// Stage row r (9 planes of site pairs, columns x0-SOFF .. x0+RX+SOFF-1
+// wrapped in x) into `slot`.  Called by a whole warp: lane 0 posts the byte
+// count of the row on the slot's mbarrier, then lanes 0..8 each copy one plane
+// (one bulk copy, or two where the window crosses the periodic seam).
 template <int STORAGE>
-__device__ __forceinline__ void issue_row(const typename Store<STORAGE>::T* __restrict__ src,
-                                          typename Store<STORAGE>::T* slot, uint64_t* bar,
+__device__ __forceinline__ void issue_row(const typename PairStore<STORAGE>::T2* __restrict__ src,
+                                          typename PairStore<STORAGE>::T2* slot, uint64_t* bar,
                                           const Geom& g, int x0, int r, int lane) {
-  using T = typename Store<STORAGE>::T;
+  using T2 = typename PairStore<STORAGE>::T2;
   constexpr int SOFF = RowsCfg<STORAGE>::SOFF;
   constexpr int SW = stage_width<STORAGE>();
-  if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(18 * SW * sizeof(T)));
+  if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(9 * SW * sizeof(T2)));
   __syncwarp();
-  if (lane >= 18) return;
+  if (lane >= 9) return;
   const int ys = stencil_row(r, g.ny, g.boundary);
   const int gx0 = x0 - SOFF;
-  int c_split, g_first;  // columns [0, c_split) from g_first, [c_split, SW) from column 0
+  int c_split, g_first;  // sites [0, c_split) from g_first, [c_split, SW) from column 0
   if (gx0 < 0) {
     c_split = -gx0;
     g_first = g.nx + gx0;
@@ -136,31 +144,32 @@ __device__ __forceinline__ void issue_row(const typename Store<STORAGE>::T* __re
     c_split = SW;
     g_first = gx0;
   }
-  const T* pl = src + (long long)ys * g.pitch + (long long)lane * g.plane;
-  T* d = slot + lane * SW;
-  bulk_g2s(d, pl + g_first, (uint32_t)(c_split * sizeof(T)), bar);
-  if (c_split < SW) bulk_g2s(d + c_split, pl, (uint32_t)((SW - c_split) * sizeof(T)), bar);
+  const T2* pl = src + (long long)lane * g.plane + (long long)ys * g.pitch;
+  T2* d = slot + lane * SW;
+  bulk_g2s(d, pl + g_first, (uint32_t)(c_split * sizeof(T2)), bar);
+  if (c_split < SW) bulk_g2s(d + c_split, pl, (uint32_t)((SW - c_split) * sizeof(T2)), bar);
 }
 
 template <int STORAGE>
 __global__ void __launch_bounds__(RTHREADS, RowsCfg<STORAGE>::MINB)
-    k_rows(const typename Store<STORAGE>::T* __restrict__ src,
-           typename Store<STORAGE>::T* __restrict__ dst, Geom g,
+    k_rows(const typename PairStore<STORAGE>::T2* __restrict__ src,
+           typename PairStore<STORAGE>::T2* __restrict__ dst, Geom g,
            Phys<typename Store<STORAGE>::C> ph, int nstrips, int kranges, Status* status) {
-  using S = Store<STORAGE>;
-  using T = typename S::T;
-  using C = typename S::C;
+  using PS = PairStore<STORAGE>;
+  using T2 = typename PS::T2;
+  using C = typename Store<STORAGE>::C;
+  using P = typename PairOf<C>::P;
   constexpr int SOFF = RowsCfg<STORAGE>::SOFF;
   constexpr int NSLOT = RowsCfg<STORAGE>::NSLOT;
   constexpr int SW = stage_width<STORAGE>();
-  constexpr int SLOT = 18 * SW;
+  constexpr int SLOT = 9 * SW;
   constexpr int EXT = RX + 4;
 
   extern __shared__ __align__(128) unsigned char smem[];
-  T* stage = reinterpret_cast<T*>(smem);
-  C* rowbuf0 = reinterpret_cast<C*>(smem + (size_t)NSLOT * SLOT * sizeof(T));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)NSLOT * SLOT * sizeof(T) +
-                                               2 * 4 * EXT * sizeof(C));
+  T2* stage = reinterpret_cast<T2*>(smem);
+  P* rowbuf0 = reinterpret_cast<P*>(smem + (size_t)NSLOT * SLOT * sizeof(T2));
+  uint64_t* bars =
+      reinterpret_cast<uint64_t*>(smem + (size_t)NSLOT * SLOT * sizeof(T2) + 2 * 2 * EXT * sizeof(P));
   __shared__ int s_abort;
 
   const int tid = threadIdx.x;
@@ -189,34 +198,41 @@ __global__ void __launch_bounds__(RTHREADS, RowsCfg<STORAGE>::MINB)
                          ylo - 2 + issued, lane);
   }
 
-  // per-thread column data
   const bool compute = warp < 4;
   const int t = compute ? tid : 0;
   const int x = x0 + t;
   const bool active = compute && (x < g.nx);
-  const int xm = (x == 0) ? g.nx - 1 : x - 1;
-  const int xp = (x >= g.nx - 1) ? 0 : x + 1;
-  // rho/psi column of this thread: its own column (compute warps) or a halo column
-  int ecol;  // index into the ext row [0, EXT): column x0 - 2 + ecol
+  int ecol;  // rho/psi column in the ext row [0, RX+4): column x0 - 2 + ecol
   if (compute)
     ecol = t + 2;
   else
     ecol = (lane < 2) ? lane : (lane < 4 ? RX + lane : -1);
+  const int xm = (x == 0) ? g.nx - 1 : x - 1;
+  const int xp = (x >= g.nx - 1) ? 0 : x + 1;
+  // push targets at columns x-1, x, x+1 (wrapped), row 0, plane 0
+  T2* const Pm = dst + xm;
+  T2* const P0 = dst + x;
+  T2* const Pp = dst + xp;
 
-  // accumulators: index k <-> row r - 2 + k of the row r just staged
-  C Sx[2][5], Sy[2][5], Cx[2][4], Cy[2][4];
+  // per-species constants as pairs
+  const P Wa = pmk(ph.Wpsi[0][0], ph.Wpsi[1][0]), Wb = pmk(ph.Wpsi[0][1], ph.Wpsi[1][1]);
+  const P Wc = pmk(ph.Wpsi[0][2], ph.Wpsi[1][2]), Wd = pmk(ph.Wpsi[0][3], ph.Wpsi[1][3]);
+  const P We = pmk(ph.Wpsi[0][4], ph.Wpsi[1][4]);
+  const P W2c = pmk(ph.W2psi[0][0], ph.W2psi[1][0]), W2d = pmk(ph.W2psi[0][1], ph.W2psi[1][1]);
+  const P W2e = pmk(ph.W2psi[0][2], ph.W2psi[1][2]);
+  const P rho_ref = pmk(ph.rho_ref[0], ph.rho_ref[1]);
+  const P mrho0E = pmk(-ph.rho0 * ph.E[0], -ph.rho0 * ph.E[1]);
+  const P om = pmk(ph.omega[0], ph.omega[1]);
+
+  // accumulators (pairs): index k <-> row r - 2 + k of the row r just staged
+  P Sx[5], Sy[5], Cx[4], Cy[4];
 #pragma unroll
-  for (int s = 0; s < 2; ++s) {
+  for (int k = 0; k < 5; ++k) Sx[k] = Sy[k] = pbc(C(0));
 #pragma unroll
-    for (int k = 0; k < 5; ++k) Sx[s][k] = Sy[s][k] = C(0);
+  for (int k = 0; k < 4; ++k) Cx[k] = Cy[k] = pbc(C(0));
+  P lag_rho[3], lag_psi[3];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) Cx[s][k] = Cy[s][k] = C(0);
-  }
-  C lag_rho[2][3], lag_drho[2][3], lag_psi[2][3];
-#pragma unroll
-  for (int s = 0; s < 2; ++s)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) lag_rho[s][k] = lag_drho[s][k] = lag_psi[s][k] = C(0);
+  for (int k = 0; k < 3; ++k) lag_rho[k] = lag_psi[k] = pbc(C(0));
   int bad = 0;
 
   int q = 0;
@@ -227,29 +243,20 @@ __global__ void __launch_bounds__(RTHREADS, RowsCfg<STORAGE>::MINB)
       atomicExch(&status->timeout, 1u);
       s_abort = 1;
     }
-    const T* srow = stage + slot * SLOT;
-    C* rowbuf = rowbuf0 + (q & 1) * 4 * EXT;
-    C* rA = rowbuf;
-    C* rB = rowbuf + EXT;
-    C* pA = rowbuf + 2 * EXT;
-    C* pB = rowbuf + 3 * EXT;
-    // ---- densities and pseudo-potentials of this row ----
-    C my_rho[2] = {C(0), C(0)}, my_drho[2] = {C(0), C(0)}, my_psi[2] = {C(0), C(0)};
+    const T2* srow = stage + slot * SLOT;
+    P* rbuf = rowbuf0 + (q & 1) * 2 * EXT;  // [0, EXT): rho pairs; [EXT, 2 EXT): psi pairs
+    // ---- density and pseudo-potential pair of this thread's column ----
+    P my_rho = pbc(C(0)), my_psi = pbc(C(0));
     if (ecol >= 0) {
-      const int sc = ecol - 2 + SOFF;
+      const T2* p = srow + (ecol - 2 + SOFF);
+      P a = PS::ld(p[0]);
 #pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        C a = C(0);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) a += S::ld(srow[(s * 9 + i) * SW + sc]);
-        my_drho[s] = a;
-        my_rho[s] = ph.rho_ref[s] + a;
-        my_psi[s] = ph.rho0 * (C(1) - ph.E[s] * exp_c<C>(-a * ph.inv_rho0));
-      }
-      rA[ecol] = my_rho[0];
-      rB[ecol] = my_rho[1];
-      pA[ecol] = my_psi[0];
-      pB[ecol] = my_psi[1];
+      for (int i = 1; i < 9; ++i) a = padd(a, PS::ld(p[i * SW]));
+      my_rho = padd(rho_ref, a);
+      const P ex = pmk(exp_c<C>(-a.x * ph.inv_rho0), exp_c<C>(-a.y * ph.inv_rho0));
+      my_psi = pfma(mrho0E, ex, pbc(ph.rho0));
+      rbuf[ecol] = my_rho;
+      rbuf[EXT + ecol] = my_psi;
     }
     __syncthreads();
     if (s_abort) break;
@@ -263,126 +270,138 @@ __global__ void __launch_bounds__(RTHREADS, RowsCfg<STORAGE>::MINB)
     if (compute) {
       const int e = ecol;
       // ---- this row's contribution to the force stencil of rows r-2 .. r+2 ----
-#pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        const C* pp = s == 0 ? pA : pB;
-        const C m2 = pp[e - 2], m1 = pp[e - 1], p1 = pp[e + 1], p2 = pp[e + 2];
-        const C c0 = my_psi[s];
-        const C D1 = p1 - m1, D2 = p2 - m2, P1 = p1 + m1, P2 = p2 + m2;
-        const C T0 = ph.Wpsi[s][0] * D1 + ph.W2psi[s][0] * D2;
-        const C T1 = ph.Wpsi[s][1] * D1 + ph.W2psi[s][1] * D2;
-        const C T2 = ph.Wpsi[s][3] * D1 + ph.W2psi[s][2] * D2;
-        const C H1 = ph.Wpsi[s][0] * c0 + ph.Wpsi[s][1] * P1 + ph.Wpsi[s][3] * P2;
-        const C H2 = ph.Wpsi[s][2] * c0 + ph.Wpsi[s][3] * P1 + ph.Wpsi[s][4] * P2;
-        Sx[s][0] += T2;
-        Sx[s][1] += T1;
-        Sx[s][2] += T0;
-        Sx[s][3] += T1;
-        Sx[s][4] = T2;
-        Sy[s][0] += C(2) * H2;
-        Sy[s][1] += H1;
-        Sy[s][3] -= H1;
-        Sy[s][4] = -C(2) * H2;
-        // inter-species term of species s reads the other species' density
-        const C* ro = s == 0 ? rB : rA;
-        const C om1 = ro[e - 1], op1 = ro[e + 1];
-        const C oc = my_rho[1 - s];
-        const C E1 = op1 - om1, Q1 = op1 + om1;
-        const C X0 = ph.gw[0] * E1, X1 = ph.gw[1] * E1;
-        const C K = ph.gw[0] * oc + ph.gw[1] * Q1;
-        Cx[s][1] += X1;
-        Cx[s][2] += X0;
-        Cx[s][3] = X1;
-        Cy[s][1] += K;
-        Cy[s][3] = -K;
-        lag_rho[s][2] = my_rho[s];
-        lag_drho[s][2] = my_drho[s];
-        lag_psi[s][2] = my_psi[s];
+      {
+        const P* pp = rbuf + EXT;
+        const P m2 = pp[e - 2], m1 = pp[e - 1], p1 = pp[e + 1], p2 = pp[e + 2];
+        const P D1 = psub(p1, m1), D2 = psub(p2, m2), P1 = padd(p1, m1), P2 = padd(p2, m2);
+        const P T0 = pfma(Wa, D1, pmul(W2c, D2));
+        const P T1 = pfma(Wb, D1, pmul(W2d, D2));
+        const P T2 = pfma(Wd, D1, pmul(W2e, D2));
+        const P H1 = pfma(Wa, my_psi, pfma(Wb, P1, pmul(Wd, P2)));
+        const P H2 = pfma(Wc, my_psi, pfma(Wd, P1, pmul(We, P2)));
+        Sx[0] = padd(Sx[0], T2);
+        Sx[1] = padd(Sx[1], T1);
+        Sx[2] = padd(Sx[2], T0);
+        Sx[3] = padd(Sx[3], T1);
+        Sx[4] = T2;
+        Sy[0] = pfma(pbc(C(2)), H2, Sy[0]);
+        Sy[1] = padd(Sy[1], H1);
+        Sy[3] = psub(Sy[3], H1);
+        Sy[4] = pmul(pbc(C(-2)), H2);
+        // inter-species term: the other species' density (the swapped pair) on belt 1
+        const P* ro = rbuf;
+        const P rm1 = ro[e - 1], rp1 = ro[e + 1];
+        const P E1 = pswap(psub(rp1, rm1)), Q1 = pswap(padd(rp1, rm1));
+        const P X0 = pmul(pbc(ph.gw[0]), E1), X1 = pmul(pbc(ph.gw[1]), E1);
+        const P K = pfma(pbc(ph.gw[0]), pswap(my_rho), pmul(pbc(ph.gw[1]), Q1));
+        Cx[1] = padd(Cx[1], X1);
+        Cx[2] = padd(Cx[2], X0);
+        Cx[3] = X1;
+        Cy[1] = padd(Cy[1], K);
+        Cy[3] = psub(pbc(C(0)), K);
+        lag_rho[2] = my_rho;
+        lag_psi[2] = my_psi;
       }
 
       // ---- row o = r - 2 is complete: collide and push ----
       if (q >= 4 && active) {
         const int o = ylo + q - 4;
         const int oslot = slot >= 2 ? slot - 2 : slot + NSLOT - 2;
-        const T* orow = stage + oslot * SLOT + t + SOFF;
-        C d[2][9];
+        const T2* orow = stage + oslot * SLOT + t + SOFF;
+        P d[9];
 #pragma unroll
-        for (int s = 0; s < 2; ++s)
-#pragma unroll
-          for (int i = 0; i < 9; ++i) d[s][i] = S::ld(orow[(s * 9 + i) * SW]);
-        C rho[2], drho[2], Fx[2], Fy[2];
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-          rho[s] = lag_rho[s][0];
-          drho[s] = lag_drho[s][0];
-          Fx[s] = -lag_psi[s][0] * Sx[s][0] - rho[s] * Cx[s][0];
-          Fy[s] = -lag_psi[s][0] * Sy[s][0] - rho[s] * Cy[s][0];
+        for (int i = 0; i < 9; ++i) d[i] = PS::ld(orow[i * SW]);
+        const P rho = lag_rho[0];
+        const P drho = psub(rho, rho_ref);
+        // G = -F: F_s = -psi_s S_s - rho_s C_s
+        const P Gx = pfma(lag_psi[0], Sx[0], pmul(rho, Cx[0]));
+        const P Gy = pfma(lag_psi[0], Sy[0], pmul(rho, Cy[0]));
+        const P jx = padd(padd(psub(d[1], d[3]), psub(d[5], d[6])), psub(d[8], d[7]));
+        const P jy = padd(padd(psub(d[2], d[4]), psub(d[5], d[8])), psub(d[6], d[7]));
+        // common velocity u = sum_s j_s/tau_s / sum_s rho_s/tau_s
+        const P rw = pmul(rho, om), jxw = pmul(jx, om), jyw = pmul(jy, om);
+        const C inv = div_c<C>(C(1), rw.x + rw.y);
+        const C ux = (jxw.x + jxw.y) * inv, uy = (jyw.x + jyw.y) * inv;
+        // shifted velocity v_s = u + tau_s F_s / rho_s = u - (tau_s/rho_s) G_s
+        P k = pbc(C(0));
+        if (rho.x > C(0)) k.x = -div_c<C>(ph.tau[0], rho.x); else ++bad;
+        if (rho.y > C(0)) k.y = -div_c<C>(ph.tau[1], rho.y); else ++bad;
+        const P vx = pfma(k, Gx, pbc(ux));
+        const P vy = pfma(k, Gy, pbc(uy));
+        // BGK relaxation toward the shifted equilibrium (factored form, see lb_site.cuh)
+        {
+          const P keep = psub(pbc(C(1)), om);
+          const P v2 = pfma(vx, vx, pmul(vy, vy));
+          const P tt = pfma(pmul(pbc(C(-1.5)), rho), v2, drho);
+          const P B0 = pmul(pmul(om, pbc(wq<C>(0))), tt);
+          const P B1 = pmul(pmul(om, pbc(wq<C>(1))), tt);
+          const P B2 = pmul(pmul(om, pbc(wq<C>(5))), tt);
+          const P a1 = pmul(pmul(om, pbc(C(3) * wq<C>(1))), rho);
+          const P b1 = pmul(pmul(om, pbc(C(4.5) * wq<C>(1))), rho);
+          const P a2 = pmul(pmul(om, pbc(C(3) * wq<C>(5))), rho);
+          const P b2 = pmul(pmul(om, pbc(C(4.5) * wq<C>(5))), rho);
+          d[0] = pfma(keep, d[0], B0);
+          const P ex = pfma(pmul(b1, vx), vx, B1), ax = pmul(a1, vx);
+          const P ey = pfma(pmul(b1, vy), vy, B1), ay = pmul(a1, vy);
+          d[1] = pfma(keep, d[1], padd(ex, ax));
+          d[3] = pfma(keep, d[3], psub(ex, ax));
+          d[2] = pfma(keep, d[2], padd(ey, ay));
+          d[4] = pfma(keep, d[4], psub(ey, ay));
+          const P s1 = padd(vx, vy), s2 = psub(vx, vy);
+          const P e1 = pfma(pmul(b2, s1), s1, B2), ad1 = pmul(a2, s1);
+          const P e2 = pfma(pmul(b2, s2), s2, B2), ad2 = pmul(a2, s2);
+          d[5] = pfma(keep, d[5], padd(e1, ad1));
+          d[7] = pfma(keep, d[7], psub(e1, ad1));
+          d[8] = pfma(keep, d[8], padd(e2, ad2));
+          d[6] = pfma(keep, d[6], psub(e2, ad2));
         }
-        C jx[2], jy[2];
-        momenta<C>(d, jx, jy);
-        C vx[2], vy[2];
-        shifted_velocities<C>(ph, rho, jx, jy, Fx, Fy, vx, vy, bad);
-        bgk<C>(ph, d, drho, rho, vx, vy);
-
         const bool wall = (g.boundary == LB_COUETTE) && (o == 0 || o == g.ny - 1);
         if (!wall) {
-          const int om = (o == 0) ? g.ny - 1 : o - 1;
-          const int op = (o == g.ny - 1) ? 0 : o + 1;
-          T* Rm = dst + (long long)om * g.pitch;
-          T* R0 = dst + (long long)o * g.pitch;
-          T* Rp = dst + (long long)op * g.pitch;
-#pragma unroll
-          for (int s = 0; s < 2; ++s) {
-            const long long b = (long long)(s * 9) * g.plane;
-            R0[b + 0 * g.plane + x] = S::st(d[s][0]);
-            R0[b + 1 * g.plane + xp] = S::st(d[s][1]);
-            Rp[b + 2 * g.plane + x] = S::st(d[s][2]);
-            R0[b + 3 * g.plane + xm] = S::st(d[s][3]);
-            Rm[b + 4 * g.plane + x] = S::st(d[s][4]);
-            Rp[b + 5 * g.plane + xp] = S::st(d[s][5]);
-            Rp[b + 6 * g.plane + xm] = S::st(d[s][6]);
-            Rm[b + 7 * g.plane + xm] = S::st(d[s][7]);
-            Rm[b + 8 * g.plane + xp] = S::st(d[s][8]);
-          }
+          // row and plane offsets are the same for every thread of the CTA
+          const int om_ = (o == 0) ? g.ny - 1 : o - 1;
+          const int op_ = (o == g.ny - 1) ? 0 : o + 1;
+          const long long Om = (long long)om_ * g.pitch, O0 = (long long)o * g.pitch,
+                          Op = (long long)op_ * g.pitch;
+          P0[O0] = PS::st(d[0]);
+          Pp[1 * g.plane + O0] = PS::st(d[1]);
+          P0[2 * g.plane + Op] = PS::st(d[2]);
+          Pm[3 * g.plane + O0] = PS::st(d[3]);
+          P0[4 * g.plane + Om] = PS::st(d[4]);
+          Pp[5 * g.plane + Op] = PS::st(d[5]);
+          Pm[6 * g.plane + Op] = PS::st(d[6]);
+          Pm[7 * g.plane + Om] = PS::st(d[7]);
+          Pp[8 * g.plane + Om] = PS::st(d[8]);
         } else {
 #pragma unroll
-          for (int s = 0; s < 2; ++s)
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-              const int yd = o + Q9::cy(i);
-              if (yd < 0 || yd >= g.ny) {
-                const C Uw = (yd >= g.ny) ? ph.Uwall : -ph.Uwall;
-                const C val = d[s][i] - wall_term<C>(i, rho[s], Uw);
-                dst[(long long)(s * 9 + Q9::opp(i)) * g.plane + (long long)o * g.pitch + x] = S::st(val);
-              } else {
-                const int xd = Q9::cx(i) == 0 ? x : (Q9::cx(i) > 0 ? xp : xm);
-                dst[(long long)(s * 9 + i) * g.plane + (long long)yd * g.pitch + xd] = S::st(d[s][i]);
-              }
+          for (int i = 0; i < 9; ++i) {
+            const int yd = o + Q9::cy(i);
+            if (yd < 0 || yd >= g.ny) {
+              // Ladd: back along opp(i), less 2 w_i rho_s (c_i . U_w)/cs2 per species
+              const C Uw = (yd >= g.ny) ? ph.Uwall : -ph.Uwall;
+              const P val = pfma(pbc(-C(6) * wq<C>(i) * C(Q9::cx(i)) * Uw), rho, d[i]);
+              P0[(long long)Q9::opp(i) * g.plane + (long long)o * g.pitch] = PS::st(val);
+            } else {
+              T2* Pc = Q9::cx(i) == 0 ? P0 : (Q9::cx(i) > 0 ? Pp : Pm);
+              Pc[(long long)i * g.plane + (long long)yd * g.pitch] = PS::st(d[i]);
             }
+          }
         }
       }
       // ---- slide the windows by one row ----
 #pragma unroll
-      for (int s = 0; s < 2; ++s) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          Sx[s][k] = Sx[s][k + 1];
-          Sy[s][k] = Sy[s][k + 1];
-        }
-        Sy[s][4] = C(0);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          Cx[s][k] = Cx[s][k + 1];
-          Cy[s][k] = Cy[s][k + 1];
-        }
-        Cy[s][3] = C(0);
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          lag_rho[s][k] = lag_rho[s][k + 1];
-          lag_drho[s][k] = lag_drho[s][k + 1];
-          lag_psi[s][k] = lag_psi[s][k + 1];
-        }
+      for (int k = 0; k < 4; ++k) {
+        Sx[k] = Sx[k + 1];
+        Sy[k] = Sy[k + 1];
       }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        Cx[k] = Cx[k + 1];
+        Cy[k] = Cy[k + 1];
+      }
+      lag_rho[0] = lag_rho[1];
+      lag_rho[1] = lag_rho[2];
+      lag_psi[0] = lag_psi[1];
+      lag_psi[1] = lag_psi[2];
     }
     if (++slot == NSLOT) {
       slot = 0;
@@ -419,11 +438,10 @@ static int resident_blocks() {
   return cached;
 }
 
-static int align_elems(int storage) { return 16 / (int)elem_size(storage); }
-
 bool rows_supported(const Geom& g, int storage) {
-  if (elem_size(storage) == 0) return false;
-  const int a = align_elems(storage);
+  const int pair_bytes = 2 * (int)elem_size(storage);
+  if (pair_bytes == 0) return false;
+  const int a = pair_bytes >= 16 ? 1 : 16 / pair_bytes;  // sites per 16 bytes
   int sw = 0, resident = 0;
   // (also sets the kernel's shared-memory attribute, outside any stream capture)
   switch (storage) {
@@ -439,7 +457,7 @@ bool rows_supported(const Geom& g, int storage) {
 template <int STORAGE>
 static cudaError_t rows_t(const void* src, void* dst, const Geom& g, const PhysD& pd,
                           Status* status, cudaStream_t st) {
-  using S = Store<STORAGE>;
+  using T2 = typename PairStore<STORAGE>::T2;
   const int nstrips = (g.nx + RX - 1) / RX;
   const int resident = resident_blocks<STORAGE>();
   int k = resident / nstrips;
@@ -447,8 +465,7 @@ static cudaError_t rows_t(const void* src, void* dst, const Geom& g, const PhysD
   if (k > g.ny) k = g.ny;
   const size_t smem = rows_smem_bytes<STORAGE>();
   k_rows<STORAGE><<<nstrips * k, RTHREADS, smem, st>>>(
-      (const typename S::T*)src, (typename S::T*)dst, g, make_phys<typename S::C>(pd), nstrips, k,
-      status);
+      (const T2*)src, (T2*)dst, g, make_phys<typename Store<STORAGE>::C>(pd), nstrips, k, status);
   return cudaGetLastError();
 }
 

@@ -66,6 +66,40 @@ __device__ __forceinline__ void bgk(const Phys<C>& ph, C (&d)[2][9], const C (&d
   }
 }
 
+// The same BGK update, factored for FP32 throughput: with
+//   A_k = omega w_k rho,  B_k = omega w_k (drho - 1.5 rho v^2)   (k = |c|^2 class),
+// the relaxed deviation is (1 - omega) d_i + B_k + A_k (3 cu + 4.5 cu^2), and
+// opposite speeds share B_k + 4.5 A_k cu^2, differing only in the sign of 3 A_k cu.
+template <typename C>
+__device__ __forceinline__ void bgk_fast(const Phys<C>& ph, C (&d)[2][9], const C (&drho)[2],
+                                         const C (&rho)[2], const C (&vx)[2], const C (&vy)[2]) {
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const C om = ph.omega[s];
+    const C keep = C(1) - om;
+    const C t = drho[s] - C(1.5) * rho[s] * (vx[s] * vx[s] + vy[s] * vy[s]);
+    const C B0 = om * wq<C>(0) * t, B1 = om * wq<C>(1) * t, B2 = om * wq<C>(5) * t;
+    const C A1 = om * wq<C>(1) * rho[s], A2 = om * wq<C>(5) * rho[s];
+    const C a1 = C(3) * A1, b1 = C(4.5) * A1, a2 = C(3) * A2, b2 = C(4.5) * A2;
+    d[s][0] = keep * d[s][0] + B0;
+    // axis pairs (1,3) along x and (2,4) along y
+    const C ex = B1 + b1 * vx[s] * vx[s], ax = a1 * vx[s];
+    const C ey = B1 + b1 * vy[s] * vy[s], ay = a1 * vy[s];
+    d[s][1] = keep * d[s][1] + (ex + ax);
+    d[s][3] = keep * d[s][3] + (ex - ax);
+    d[s][2] = keep * d[s][2] + (ey + ay);
+    d[s][4] = keep * d[s][4] + (ey - ay);
+    // diagonal pairs (5,7) along (1,1) and (8,6) along (1,-1)
+    const C s1 = vx[s] + vy[s], s2 = vx[s] - vy[s];
+    const C e1 = B2 + b2 * s1 * s1, a1d = a2 * s1;
+    const C e2 = B2 + b2 * s2 * s2, a2d = a2 * s2;
+    d[s][5] = keep * d[s][5] + (e1 + a1d);
+    d[s][7] = keep * d[s][7] + (e1 - a1d);
+    d[s][8] = keep * d[s][8] + (e2 + a2d);
+    d[s][6] = keep * d[s][6] + (e2 - a2d);
+  }
+}
+
 // Ladd's moving-wall term for a link i leaving the fluid through a wall of
 // velocity (Uw, 0): the population returns reversed, reduced by
 // 2 w_i rho_s (c_i . U_w) / cs2.

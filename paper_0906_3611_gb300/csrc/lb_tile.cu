@@ -37,12 +37,11 @@ __global__ void __launch_bounds__(TTHREADS)
     const int ex = e % TEX, ey = e / TEX;
     const int gx = wrapi(x0 + ex - 2, g.nx);
     const int gy = stencil_row(y0 + ey - 2, g.ny, g.boundary);
-    const T* p = src + (long long)gy * g.pitch + gx;
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       C dr = C(0);
 #pragma unroll
-      for (int i = 0; i < 9; ++i) dr += S::ld(p[(long long)(s * 9 + i) * g.plane]);
+      for (int i = 0; i < 9; ++i) dr += S::ld(src[lidx(g, s, i, gy, gx)]);
       s_rho[s][ey][ex] = ph.rho_ref[s] + dr;
       s_psi[s][ey][ex] = ph.rho0 * (C(1) - ph.E[s] * exp_c<C>(-dr * ph.inv_rho0));
     }
@@ -59,11 +58,10 @@ __global__ void __launch_bounds__(TTHREADS)
 
   if (active) {
     C d[2][9];
-    const T* p = src + (long long)y * g.pitch + x;
 #pragma unroll
     for (int s = 0; s < 2; ++s)
 #pragma unroll
-      for (int i = 0; i < 9; ++i) d[s][i] = S::ld(p[(long long)(s * 9 + i) * g.plane]);
+      for (int i = 0; i < 9; ++i) d[s][i] = S::ld(src[lidx(g, s, i, y, x)]);
 
     C drho[2], rho[2];
 #pragma unroll
@@ -149,11 +147,11 @@ __global__ void __launch_bounds__(TTHREADS)
           if (g.boundary == LB_COUETTE && (yd < 0 || yd >= g.ny)) {
             const C Uw = (yd >= g.ny) ? ph.Uwall : -ph.Uwall;
             const C val = d[s][i] - wall_term<C>(i, rho[s], Uw);
-            dst[(long long)(s * 9 + Q9::opp(i)) * g.plane + (long long)y * g.pitch + x] = S::st(val);
+            dst[lidx(g, s, Q9::opp(i), y, x)] = S::st(val);
           } else {
             yd = wrapi(yd, g.ny);
             const int xd = wrapi(x + Q9::cx(i), g.nx);
-            dst[(long long)(s * 9 + i) * g.plane + (long long)yd * g.pitch + xd] = S::st(d[s][i]);
+            dst[lidx(g, s, i, yd, xd)] = S::st(d[s][i]);
           }
         }
     }
@@ -216,12 +214,11 @@ __global__ void __launch_bounds__(256)
   for (long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x; site < n;
        site += (long long)gridDim.x * blockDim.x) {
     const int y = (int)(site / g.nx), x = (int)(site % g.nx);
-    const T* p = src + (long long)y * g.pitch + x;
     C d[2][9];
 #pragma unroll
     for (int s = 0; s < 2; ++s)
 #pragma unroll
-      for (int i = 0; i < 9; ++i) d[s][i] = S::ld(p[(long long)(s * 9 + i) * g.plane]);
+      for (int i = 0; i < 9; ++i) d[s][i] = S::ld(src[lidx(g, s, i, y, x)]);
     C rho[2];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {

@@ -249,11 +249,11 @@ def test_full_size_sampled_sites_fp32_couette(lb):
     init = (0.7, 1.2, 0.1, 0.02)
     lat = lb.Lattice(nx, ny, _params(lb, CFG, lb.LB_F32, boundary=1, U=U, kind=1, init=init))
     lat.init_random(0).step(1)
-    raw = torch.empty((2, 9, ny, nx), dtype=torch.float32).pin_memory()
+    raw = torch.empty((9, ny, nx, 2), dtype=torch.float32).pin_memory()  # native order [i][y][x][s]
     lb.lb_get_state_raw(lat.h, raw.data_ptr())
     assert lat.status() == lb.LB_OK
     lat.close()
-    got = raw.numpy()
+    got = raw.numpy().transpose(3, 0, 1, 2)
     rho0f = oracle.init_densities(nx, ny, 0, 1, init)
     sites = inputs.sample_sites(nx, ny, 40, seed=1) + [(0, 17), (1, 900), (ny - 2, 5), (ny - 1, 2048)]
     for (ys, xs) in sites:
