@@ -27,8 +27,8 @@
 // read from DRAM once and written once; the halos (2 columns, 2+2 rows per
 // range) are served by L2 or recomputed.
 //
-// Warps 0-3 compute; warp 4 issues the bulk copies and forms rho/psi of the
-// four halo columns.  Every mbarrier wait is bounded: on timeout the kernel
+// Warps 0..NCW-1 compute; warp NCW issues the bulk copies and forms rho/psi of
+// the four halo columns.  Every mbarrier wait is bounded: on timeout the kernel
 // sets the status word, drains its own copies (bounded) and leaves.
 #include "lb_pair.cuh"
 #include "lb_rows.h"
@@ -36,8 +36,9 @@
 
 namespace lbk {
 
-constexpr int RX = 128;            // interior columns per strip
-constexpr int RTHREADS = RX + 32;  // 4 compute warps + 1 copy/halo warp
+constexpr int RX = 128;            // interior columns per strip (a multiple of 32)
+constexpr int NCW = RX / 32;       // compute warps
+constexpr int RTHREADS = RX + 32;  // compute warps + 1 copy/halo warp
 
 // SOFF: halo sites staged on each side (>= 2, a 16-byte multiple of pairs);
 // NSLOT: ring depth; MINB: CTAs per SM the register budget is sized for.
@@ -188,17 +189,17 @@ __global__ void __launch_bounds__(RTHREADS, RowsCfg<STORAGE>::MINB)
     s_abort = 0;
   }
   __syncthreads();
-  // warp 4 stages rows; a row's slot is refilled once every thread has passed
-  // the barrier of the row three later (its collision is then done)
-  const bool producer = (warp == 4);
-  int issued = 0;  // rows staged so far (same in every lane of warp 4)
+  // the last warp stages rows; a row's slot is refilled once every thread has
+  // passed the barrier of the row three later (its collision is then done)
+  const bool producer = (warp == NCW);
+  int issued = 0;  // rows staged so far (same in every lane of the producer warp)
   if (producer) {
     for (; issued < NSLOT - 3 && issued < nstage; ++issued)
       issue_row<STORAGE>(src, stage + (issued % NSLOT) * SLOT, &bars[issued % NSLOT], g, x0,
                          ylo - 2 + issued, lane);
   }
 
-  const bool compute = warp < 4;
+  const bool compute = warp < NCW;
   const int t = compute ? tid : 0;
   const int x = x0 + t;
   const bool active = compute && (x < g.nx);
@@ -362,15 +363,16 @@ __global__ void __launch_bounds__(RTHREADS, RowsCfg<STORAGE>::MINB)
           const int op_ = (o == g.ny - 1) ? 0 : o + 1;
           const long long Om = (long long)om_ * g.pitch, O0 = (long long)o * g.pitch,
                           Op = (long long)op_ * g.pitch;
-          P0[O0] = PS::st(d[0]);
-          Pp[1 * g.plane + O0] = PS::st(d[1]);
-          P0[2 * g.plane + Op] = PS::st(d[2]);
-          Pm[3 * g.plane + O0] = PS::st(d[3]);
-          P0[4 * g.plane + Om] = PS::st(d[4]);
-          Pp[5 * g.plane + Op] = PS::st(d[5]);
-          Pm[6 * g.plane + Op] = PS::st(d[6]);
-          Pm[7 * g.plane + Om] = PS::st(d[7]);
-          Pp[8 * g.plane + Om] = PS::st(d[8]);
+          // streaming (evict-first) stores: the new state is read back only next step
+          __stcs(&P0[O0], PS::st(d[0]));
+          __stcs(&Pp[1 * g.plane + O0], PS::st(d[1]));
+          __stcs(&P0[2 * g.plane + Op], PS::st(d[2]));
+          __stcs(&Pm[3 * g.plane + O0], PS::st(d[3]));
+          __stcs(&P0[4 * g.plane + Om], PS::st(d[4]));
+          __stcs(&Pp[5 * g.plane + Op], PS::st(d[5]));
+          __stcs(&Pm[6 * g.plane + Op], PS::st(d[6]));
+          __stcs(&Pm[7 * g.plane + Om], PS::st(d[7]));
+          __stcs(&Pp[8 * g.plane + Om], PS::st(d[8]));
         } else {
 #pragma unroll
           for (int i = 0; i < 9; ++i) {
