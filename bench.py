@@ -38,6 +38,11 @@ WORKLOADS = {
     "couette4096_bf16dev": (4096, 4096, 1, 0.02, 2),
     "couette4096_f16dev": (4096, 4096, 1, 0.02, 3),
 }
+BATCHES = {
+    # name: (replicas, side choices, U range, storage)
+    "batch256_f32": (256, (128, 256, 512, 1024), 0.05, 1),
+    "batch256_f16dev": (256, (128, 256, 512, 1024), 0.05, 3),
+}
 STORAGE_NAME = {0: "f64", 1: "f32", 2: "bf16dev", 3: "f16dev"}
 ELEM = {0: 8, 1: 4, 2: 2, 3: 2}
 
@@ -270,13 +275,106 @@ def run_gpu(args):
         pg.destroy_process_group()
 
 
+def batch_replicas(name):
+    """The ensemble of a batch workload: sides uniform from the choices, Couette
+    walls at U ~ U[0, Umax], seeds 0..n-1 (numpy Philox stream, seed 0)."""
+    import numpy as np
+    n, sides, umax, storage = BATCHES[name]
+    g = np.random.Generator(np.random.Philox(key=0))
+    side = g.choice(np.array(sides), size=n)
+    U = g.uniform(0.0, umax, size=n)
+    return [(int(side[k]), float(U[k]), k) for k in range(n)], storage
+
+
+def run_batch(args):
+    """Batched ensemble: all replicas in one persistent launch per step, against
+    the same replicas stepped one lattice at a time (sequential launches)."""
+    import torch
+
+    from paper_0906_3611_gb300 import lb
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    reps, storage = batch_replicas(args.workload)
+    stream = torch.cuda.Stream()
+
+    def prm(U):
+        return lb.make_params(**PHYS, boundary=lb.LB_COUETTE, U_wall=U, storage=storage,
+                              rho_ref=(0.88, 0.44), init_kind=lb.LB_INIT_BERNOULLI, init=INIT)
+
+    sites = sum(side * side for side, _, _ in reps)
+    b = lb.Batch(len(reps), storage, stream)
+    budget = args.warmup + args.steps + 64
+    for side, U, seed in reps:
+        b.add(side, side, prm(U), seed, budget)
+    rows = b.autotune(2)
+    for k in range(len(reps)):  # the autotuner spent budget: refill it
+        b.set_steps(k, args.warmup + args.steps)
+    sampler = ClockSampler(local)
+    sampler.start()
+    b.run(args.warmup)
+    stream.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    b.run(args.steps)
+    end.record(stream)
+    end.synchronize()
+    clocks = sampler.stop()
+    ms = start.elapsed_time(end)
+    rem, done = b.poll()
+    status = b.status()
+    b.close()
+    value = sites * args.steps / (ms * 1e-3) / 1e6
+
+    # the same replicas, one lattice at a time (each replica's steps in one lb_step)
+    seq_steps = max(1, args.steps // 4)
+    lats = []
+    t_seq = 0.0
+    for side, U, seed in reps:
+        lat = lb.Lattice(side, side, prm(U), stream=stream).init_random(seed)
+        lat.step(3)
+        stream.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        lat.step(seq_steps)
+        s1.record(stream)
+        s1.synchronize()
+        t_seq += s0.elapsed_time(s1)
+        lat.close()
+    seq_value = sites * seq_steps / (t_seq * 1e-3) / 1e6
+    es = ELEM[storage]
+    bytes_per_site = 2 * 18 * es
+    achieved = bytes_per_site * sites / (ms * 1e-3 / args.steps) / 1e9
+    peak, peak_kind = peaks()
+    if rank == 0:
+        line = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": args.workload, "replicas": len(reps), "sites": sites,
+                           "sides": sorted(set(s for s, _, _ in reps)),
+                           "storage": STORAGE_NAME[storage], "boundary": "couette",
+                           "U_wall": "uniform[0, 0.05]", "rows_per_item": rows,
+                           "l2": f"inputs larger than L2 ({sites * 18 * es / 1e9:.1f} GB per buffer set)"},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": None,
+                             "bytes_per_site": bytes_per_site, "peak_kind": peak_kind},
+                "sequential_single_lattice_mlups": seq_value,
+                "gpu_launches": args.steps, "clocks": clocks,
+                "status": lb.lb_strerror(status), "impl": "gb300"}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="couette4096_f32", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="couette4096_f32",
+                    choices=sorted(WORKLOADS) + sorted(BATCHES))
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -284,6 +382,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload in BATCHES:
+        run_batch(args)
     else:
         run_gpu(args)
 

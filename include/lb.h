@@ -198,6 +198,60 @@ LB_API void lb_destroy(lb_handle *h);
 LB_API int lb_observables_noalloc(const void *f, int nx, int ny, int pitch, const lb_params *p,
                                   void *cuda_stream, double *out);
 
+/* ---- Batched ensembles ----
+ * A batch advances many independent lattices (replicas) of uneven sizes
+ * together: one persistent launch of the row-streaming kernel per step walks a
+ * work list of (replica, strip, row range) items, and runs of steps replay a
+ * captured CUDA graph.  Each replica has its own couplings, boundary, seed
+ * and step budget; a replica whose budget is spent stays unchanged while the
+ * others keep stepping.  Replicas can be added and removed between runs (the
+ * serving loop admits requests into free slots).  All replicas of a batch use
+ * the batch's storage type; every replica needs nx >= 8 and nx a multiple of
+ * 16 bytes' worth of site pairs (2 sites for FP32, 4 for the 16-bit storages).
+ * Calls enqueue on the batch's stream; the ones returning host data sync it. */
+typedef struct lb_batch lb_batch;
+
+/* Empty batch of `capacity` slots for `storage`; its work tables live on the
+ * current device. */
+LB_API int lb_batch_create(int capacity, int storage, void *cuda_stream, lb_batch **out);
+
+/* Add a replica: allocates its two population buffers, fills them with the
+ * seeded recipe of p (as lb_init_random), and gives it `steps` steps of
+ * budget.  *slot receives its slot.  LB_EBUSY when every slot is taken. */
+LB_API int lb_batch_add(lb_batch *b, int nx, int ny, const lb_params *p, uint64_t seed,
+                        int64_t steps, int *slot);
+
+/* Remove a replica and free its buffers (synchronises). */
+LB_API int lb_batch_remove(lb_batch *b, int slot);
+
+/* Replace a replica's remaining step budget. */
+LB_API int lb_batch_set_steps(lb_batch *b, int slot, int64_t steps);
+
+/* Enqueue n step launches; each advances every replica with budget left by
+ * one step of Eq. (be) and spends one step of its budget.  Asynchronous. */
+LB_API int lb_batch_run(lb_batch *b, int64_t n);
+
+/* Synchronise and read, per slot, the remaining budget and the steps taken
+ * (-1 for empty slots); either pointer may be NULL; arrays of `capacity`. */
+LB_API int lb_batch_poll(lb_batch *b, int64_t *remaining, int64_t *steps_done);
+
+/* lb_observables / lb_get_state of one replica (synchronise). */
+LB_API int lb_batch_observables(lb_batch *b, int slot, double *rho, double *u, double *stress,
+                                double *mass);
+LB_API int lb_batch_get_state(lb_batch *b, int slot, double *f);
+
+/* Pick the rows per work item (16 ... 256) that time fastest on the current
+ * replicas; each candidate runs steps_per_candidate + 1 real steps of every
+ * replica with budget left (spending that budget).  *rows_per_item receives
+ * the choice (may be NULL). */
+LB_API int lb_batch_autotune(lb_batch *b, int steps_per_candidate, int *rows_per_item);
+
+/* Read and clear the batch's device status word (as lb_status). */
+LB_API int lb_batch_status(lb_batch *b);
+
+/* Free the batch and every replica's buffers. */
+LB_API void lb_batch_destroy(lb_batch *b);
+
 /* Static text for an error code. */
 LB_API const char *lb_strerror(int code);
 

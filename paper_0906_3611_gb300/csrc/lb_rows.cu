@@ -121,7 +121,8 @@ __device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, u
 // Stage row r (9 planes of site pairs, columns x0-SOFF .. x0+RX+SOFF-1
 // wrapped in x) into `slot`.  Called by a whole warp: lane 0 posts the byte
 // count of the row on the slot's mbarrier, then lanes 0..8 each copy one plane
-// (one bulk copy, or two where the window crosses the periodic seam).
+// as one bulk copy per contiguous run of the periodic window (one run, or two
+// across the seam; more only for lattices narrower than the window).
 template <int STORAGE>
 __device__ __forceinline__ void issue_row(const typename PairStore<STORAGE>::T2* __restrict__ src,
                                           typename PairStore<STORAGE>::T2* slot, uint64_t* bar,
@@ -133,29 +134,30 @@ __device__ __forceinline__ void issue_row(const typename PairStore<STORAGE>::T2*
   __syncwarp();
   if (lane >= 9) return;
   const int ys = stencil_row(r, g.ny, g.boundary);
-  const int gx0 = x0 - SOFF;
-  int c_split, g_first;  // sites [0, c_split) from g_first, [c_split, SW) from column 0
-  if (gx0 < 0) {
-    c_split = -gx0;
-    g_first = g.nx + gx0;
-  } else if (gx0 + SW > g.nx) {
-    c_split = g.nx - gx0;
-    g_first = gx0;
-  } else {
-    c_split = SW;
-    g_first = gx0;
-  }
   const T2* pl = src + (long long)lane * g.plane + (long long)ys * g.pitch;
   T2* d = slot + lane * SW;
-  bulk_g2s(d, pl + g_first, (uint32_t)(c_split * sizeof(T2)), bar);
-  if (c_split < SW) bulk_g2s(d + c_split, pl, (uint32_t)((SW - c_split) * sizeof(T2)), bar);
+  int gx = x0 - SOFF;
+  if (gx < 0) gx += g.nx;
+  for (int c = 0; c < SW;) {
+    const int len = min(SW - c, g.nx - gx);
+    bulk_g2s(d + c, pl + gx, (uint32_t)(len * sizeof(T2)), bar);
+    c += len;
+    gx = 0;
+  }
 }
 
+// One CTA, one work range: columns x0 .. x0+RX-1 (clipped to nx), output rows
+// ylo .. yhi-1 of the lattice (src -> dst).  `ring` is the position of the
+// next staged row in the CTA's slot ring (identical in every thread); on
+// entry every slot is free.  Returns false if a bounded wait gave up (after
+// draining the copies this range issued).
 template <int STORAGE>
-__global__ void __launch_bounds__(RTHREADS, RowsCfg<STORAGE>::MINB)
-    k_rows(const typename PairStore<STORAGE>::T2* __restrict__ src,
-           typename PairStore<STORAGE>::T2* __restrict__ dst, Geom g,
-           Phys<typename Store<STORAGE>::C> ph, int nstrips, int kranges, Status* status) {
+__device__ __forceinline__ bool rows_range(
+    const typename PairStore<STORAGE>::T2* __restrict__ src,
+    typename PairStore<STORAGE>::T2* __restrict__ dst, const Geom& g,
+    const Phys<typename Store<STORAGE>::C>& ph, int x0, int ylo, int yhi,
+    typename PairStore<STORAGE>::T2* stage, typename PairOf<typename Store<STORAGE>::C>::P* rowbuf0,
+    uint64_t* bars, int& ring, int* s_abort, Status* status, int& bad) {
   using PS = PairStore<STORAGE>;
   using T2 = typename PS::T2;
   using C = typename Store<STORAGE>::C;
@@ -166,37 +168,20 @@ __global__ void __launch_bounds__(RTHREADS, RowsCfg<STORAGE>::MINB)
   constexpr int SLOT = 9 * SW;
   constexpr int EXT = RX + 4;
 
-  extern __shared__ __align__(128) unsigned char smem[];
-  T2* stage = reinterpret_cast<T2*>(smem);
-  P* rowbuf0 = reinterpret_cast<P*>(smem + (size_t)NSLOT * SLOT * sizeof(T2));
-  uint64_t* bars =
-      reinterpret_cast<uint64_t*>(smem + (size_t)NSLOT * SLOT * sizeof(T2) + 2 * 2 * EXT * sizeof(P));
-  __shared__ int s_abort;
-
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  const int strip = blockIdx.x % nstrips;
-  const int range = blockIdx.x / nstrips;
-  const int x0 = strip * RX;
-  const int ylo = (int)((long long)range * g.ny / kranges);
-  const int yhi = (int)((long long)(range + 1) * g.ny / kranges);
   const int nstage = (yhi - ylo) + 4;  // rho rows ylo-2 .. yhi+1
-  if (yhi <= ylo) return;
 
-  if (tid == 0) {
-    for (int k = 0; k < NSLOT; ++k) mbar_init(&bars[k], 1);
-    mbar_fence_init();
-    s_abort = 0;
-  }
-  __syncthreads();
   // the last warp stages rows; a row's slot is refilled once every thread has
   // passed the barrier of the row three later (its collision is then done)
   const bool producer = (warp == NCW);
   int issued = 0;  // rows staged so far (same in every lane of the producer warp)
   if (producer) {
-    for (; issued < NSLOT - 3 && issued < nstage; ++issued)
-      issue_row<STORAGE>(src, stage + (issued % NSLOT) * SLOT, &bars[issued % NSLOT], g, x0,
+    for (; issued < NSLOT - 3 && issued < nstage; ++issued) {
+      const int rp = ring + issued;
+      issue_row<STORAGE>(src, stage + (rp % NSLOT) * SLOT, &bars[rp % NSLOT], g, x0,
                          ylo - 2 + issued, lane);
+    }
   }
 
   const bool compute = warp < NCW;
@@ -234,15 +219,15 @@ __global__ void __launch_bounds__(RTHREADS, RowsCfg<STORAGE>::MINB)
   P lag_rho[3], lag_psi[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) lag_rho[k] = lag_psi[k] = pbc(C(0));
-  int bad = 0;
 
   int q = 0;
-  int slot = 0, parity = 0;  // slot of row q and the phase parity it completes
+  int slot = ring % NSLOT, parity = (ring / NSLOT) & 1;  // slot of row q and its phase parity
+  bool ok = true;
 #pragma unroll 1
   for (; q < nstage; ++q) {
     if (!mbar_wait_bounded(&bars[slot], (uint32_t)parity)) {
       atomicExch(&status->timeout, 1u);
-      s_abort = 1;
+      *s_abort = 1;
     }
     const T2* srow = stage + slot * SLOT;
     P* rbuf = rowbuf0 + (q & 1) * 2 * EXT;  // [0, EXT): rho pairs; [EXT, 2 EXT): psi pairs
@@ -260,10 +245,14 @@ __global__ void __launch_bounds__(RTHREADS, RowsCfg<STORAGE>::MINB)
       rbuf[EXT + ecol] = my_psi;
     }
     __syncthreads();
-    if (s_abort) break;
+    if (*s_abort) {
+      ok = false;
+      break;
+    }
     // every thread has finished row q-1, so the slot of row q-3 is free
     if (producer && issued < nstage) {
-      issue_row<STORAGE>(src, stage + (issued % NSLOT) * SLOT, &bars[issued % NSLOT], g, x0,
+      const int rp = ring + issued;
+      issue_row<STORAGE>(src, stage + (rp % NSLOT) * SLOT, &bars[rp % NSLOT], g, x0,
                          ylo - 2 + issued, lane);
       ++issued;
     }
@@ -277,14 +266,14 @@ __global__ void __launch_bounds__(RTHREADS, RowsCfg<STORAGE>::MINB)
         const P D1 = psub(p1, m1), D2 = psub(p2, m2), P1 = padd(p1, m1), P2 = padd(p2, m2);
         const P T0 = pfma(Wa, D1, pmul(W2c, D2));
         const P T1 = pfma(Wb, D1, pmul(W2d, D2));
-        const P T2 = pfma(Wd, D1, pmul(W2e, D2));
+        const P T2v = pfma(Wd, D1, pmul(W2e, D2));
         const P H1 = pfma(Wa, my_psi, pfma(Wb, P1, pmul(Wd, P2)));
         const P H2 = pfma(Wc, my_psi, pfma(Wd, P1, pmul(We, P2)));
-        Sx[0] = padd(Sx[0], T2);
+        Sx[0] = padd(Sx[0], T2v);
         Sx[1] = padd(Sx[1], T1);
         Sx[2] = padd(Sx[2], T0);
         Sx[3] = padd(Sx[3], T1);
-        Sx[4] = T2;
+        Sx[4] = T2v;
         Sy[0] = pfma(pbc(C(2)), H2, Sy[0]);
         Sy[1] = padd(Sy[1], H1);
         Sy[3] = psub(Sy[3], H1);
@@ -410,29 +399,139 @@ __global__ void __launch_bounds__(RTHREADS, RowsCfg<STORAGE>::MINB)
       parity ^= 1;
     }
   }
-  if (bad) atomicAdd(&status->bad_rho, (unsigned)bad);
-  if (s_abort && producer && lane == 0) {
+  if (!ok && producer && lane == 0) {
     // drain: wait (bounded) for the rows staged but not consumed, so that no
     // copy is still writing into this CTA's shared memory when it exits
     for (int k = q; k < issued; ++k) {
+      const int rp = ring + k;
       const long long t0 = clock64();
-      while (!mbar_try_wait(&bars[k % NSLOT], (uint32_t)((k / NSLOT) & 1))) {
+      while (!mbar_try_wait(&bars[rp % NSLOT], (uint32_t)((rp / NSLOT) & 1))) {
         if (clock64() - t0 > (1LL << 31)) break;
       }
     }
   }
+  ring += nstage;
+  return ok;
 }
 
-// ---- launcher ----
-
 template <int STORAGE>
+struct RowsSmem {
+  using T2 = typename PairStore<STORAGE>::T2;
+  using P = typename PairOf<typename Store<STORAGE>::C>::P;
+  T2* stage;
+  P* rowbuf0;
+  uint64_t* bars;
+  __device__ __forceinline__ explicit RowsSmem(unsigned char* smem) {
+    constexpr int SLOT = 9 * stage_width<STORAGE>();
+    constexpr int NSLOT = RowsCfg<STORAGE>::NSLOT;
+    stage = reinterpret_cast<T2*>(smem);
+    rowbuf0 = reinterpret_cast<P*>(smem + (size_t)NSLOT * SLOT * sizeof(T2));
+    bars = reinterpret_cast<uint64_t*>(smem + (size_t)NSLOT * SLOT * sizeof(T2) +
+                                       2 * 2 * (RX + 4) * sizeof(P));
+  }
+};
+
+// Single lattice: CTA b owns strip b % nstrips and row range b / nstrips.
+template <int STORAGE>
+__global__ void __launch_bounds__(RTHREADS, RowsCfg<STORAGE>::MINB)
+    k_rows(const typename PairStore<STORAGE>::T2* __restrict__ src,
+           typename PairStore<STORAGE>::T2* __restrict__ dst, Geom g,
+           Phys<typename Store<STORAGE>::C> ph, int nstrips, int kranges, Status* status) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int s_abort;
+  RowsSmem<STORAGE> sm(smem);
+  const int strip = blockIdx.x % nstrips;
+  const int range = blockIdx.x / nstrips;
+  const int ylo = (int)((long long)range * g.ny / kranges);
+  const int yhi = (int)((long long)(range + 1) * g.ny / kranges);
+  if (yhi <= ylo) return;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < RowsCfg<STORAGE>::NSLOT; ++k) mbar_init(&sm.bars[k], 1);
+    mbar_fence_init();
+    s_abort = 0;
+  }
+  __syncthreads();
+  int ring = 0, bad = 0;
+  rows_range<STORAGE>(src, dst, g, ph, strip * RX, ylo, yhi, sm.stage, sm.rowbuf0, sm.bars, ring,
+                      &s_abort, status, bad);
+  if (bad) atomicAdd(&status->bad_rho, (unsigned)bad);
+}
+
+// Batched ensemble: a persistent grid walks a work list of (replica, strip,
+// row range) items; each replica keeps its own geometry, constants, buffer
+// parity and step budget in device memory.  The CTA that finishes the last
+// item of a replica in a launch flips its parity and spends one step of its
+// budget; replicas with no budget left are skipped.
+template <int STORAGE>
+__global__ void __launch_bounds__(RTHREADS, RowsCfg<STORAGE>::MINB)
+    k_rows_batch(ReplicaDev<typename Store<STORAGE>::C>* __restrict__ reps,
+                 const WorkItem* __restrict__ items, const int* __restrict__ n_items,
+                 Status* status) {
+  using T2 = typename PairStore<STORAGE>::T2;
+  using C = typename Store<STORAGE>::C;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int s_abort;
+  __shared__ int s_skip;
+  __shared__ WorkItem s_item;
+  __shared__ Geom s_g;
+  __shared__ Phys<C> s_ph;
+  __shared__ const T2* s_src;
+  __shared__ T2* s_dst;
+  RowsSmem<STORAGE> sm(smem);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < RowsCfg<STORAGE>::NSLOT; ++k) mbar_init(&sm.bars[k], 1);
+    mbar_fence_init();
+    s_abort = 0;
+  }
+  int ring = 0, bad = 0;
+  const int n = *n_items;
+  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    __syncthreads();  // the previous item is finished by every thread
+    if (threadIdx.x == 0) {
+      s_item = items[it];
+      const ReplicaDev<C>& R = reps[s_item.replica];
+      s_skip = R.remaining <= 0;
+      s_g = R.g;
+      s_ph = R.ph;
+      s_src = (const T2*)R.buf[R.parity];
+      s_dst = (T2*)R.buf[1 - R.parity];
+    }
+    __syncthreads();
+    if (s_skip) continue;
+    if (!rows_range<STORAGE>(s_src, s_dst, s_g, s_ph, s_item.x0, s_item.ylo, s_item.yhi, sm.stage,
+                             sm.rowbuf0, sm.bars, ring, &s_abort, status, bad))
+      break;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      ReplicaDev<C>& R = reps[s_item.replica];
+      const unsigned prev = atomicAdd(&R.done, 1u);
+      if (prev + 1 == (unsigned)R.nitems) {  // the last item of this replica in this step
+        R.done = 0;
+        R.parity ^= 1;
+        R.remaining -= 1;
+        R.t += 1;
+      }
+    }
+  }
+  if (bad) atomicAdd(&status->bad_rho, (unsigned)bad);
+}
+
+// ---- launchers ----
+
+template <int STORAGE, bool BATCH>
 static int resident_blocks() {
   static int cached = -1;
   if (cached < 0) {
     const size_t smem = rows_smem_bytes<STORAGE>();
-    cudaFuncSetAttribute(k_rows<STORAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0, dev = 0, sms = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows<STORAGE>, RTHREADS, smem);
+    if (BATCH) {
+      cudaFuncSetAttribute(k_rows_batch<STORAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows_batch<STORAGE>, RTHREADS, smem);
+    } else {
+      cudaFuncSetAttribute(k_rows<STORAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows<STORAGE>, RTHREADS, smem);
+    }
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cached = per_sm * sms;
@@ -440,29 +539,41 @@ static int resident_blocks() {
   return cached;
 }
 
-bool rows_supported(const Geom& g, int storage) {
+static int resident(int storage, bool batch) {
+  switch (storage) {
+    case LB_F64: return batch ? resident_blocks<LB_F64, true>() : resident_blocks<LB_F64, false>();
+    case LB_F32: return batch ? resident_blocks<LB_F32, true>() : resident_blocks<LB_F32, false>();
+    case LB_BF16_DEV:
+      return batch ? resident_blocks<LB_BF16_DEV, true>() : resident_blocks<LB_BF16_DEV, false>();
+    case LB_F16_DEV:
+      return batch ? resident_blocks<LB_F16_DEV, true>() : resident_blocks<LB_F16_DEV, false>();
+  }
+  return 0;
+}
+
+int rows_strip_width() { return RX; }
+
+bool rows_geometry_ok(const Geom& g, int storage) {
   const int pair_bytes = 2 * (int)elem_size(storage);
   if (pair_bytes == 0) return false;
   const int a = pair_bytes >= 16 ? 1 : 16 / pair_bytes;  // sites per 16 bytes
-  int sw = 0, resident = 0;
-  // (also sets the kernel's shared-memory attribute, outside any stream capture)
-  switch (storage) {
-    case LB_F64: sw = stage_width<LB_F64>(); resident = resident_blocks<LB_F64>(); break;
-    case LB_F32: sw = stage_width<LB_F32>(); resident = resident_blocks<LB_F32>(); break;
-    case LB_BF16_DEV: sw = stage_width<LB_BF16_DEV>(); resident = resident_blocks<LB_BF16_DEV>(); break;
-    case LB_F16_DEV: sw = stage_width<LB_F16_DEV>(); resident = resident_blocks<LB_F16_DEV>(); break;
-  }
-  // 16-byte aligned rows and seams, at most one periodic seam per window
-  return resident > 0 && (g.nx % a == 0) && (g.pitch % a == 0) && (g.nx >= sw) && (g.ny >= 5);
+  // 16-byte aligned rows and seams; the periodic window may wrap several times
+  return (g.nx % a == 0) && (g.pitch % a == 0) && (g.nx >= 8) && (g.ny >= 5);
 }
+
+bool rows_supported(const Geom& g, int storage) {
+  // (also sets the kernels' shared-memory attributes, outside any stream capture)
+  return rows_geometry_ok(g, storage) && resident(storage, false) > 0 && resident(storage, true) > 0;
+}
+
+int rows_batch_grid(int storage) { return resident(storage, true); }
 
 template <int STORAGE>
 static cudaError_t rows_t(const void* src, void* dst, const Geom& g, const PhysD& pd,
                           Status* status, cudaStream_t st) {
   using T2 = typename PairStore<STORAGE>::T2;
   const int nstrips = (g.nx + RX - 1) / RX;
-  const int resident = resident_blocks<STORAGE>();
-  int k = resident / nstrips;
+  int k = resident(STORAGE, false) / nstrips;
   if (k < 1) k = 1;
   if (k > g.ny) k = g.ny;
   const size_t smem = rows_smem_bytes<STORAGE>();
@@ -478,6 +589,26 @@ cudaError_t launch_step_rows(int storage, const void* src, void* dst, const Geom
     case LB_F32: return rows_t<LB_F32>(src, dst, g, ph, status, st);
     case LB_BF16_DEV: return rows_t<LB_BF16_DEV>(src, dst, g, ph, status, st);
     case LB_F16_DEV: return rows_t<LB_F16_DEV>(src, dst, g, ph, status, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int STORAGE>
+static cudaError_t rows_batch_t(void* reps, const WorkItem* items, const int* n_items, int grid,
+                                Status* status, cudaStream_t st) {
+  using C = typename Store<STORAGE>::C;
+  k_rows_batch<STORAGE><<<grid, RTHREADS, rows_smem_bytes<STORAGE>(), st>>>(
+      (ReplicaDev<C>*)reps, items, n_items, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_rows_batch(int storage, void* reps, const WorkItem* items,
+                                   const int* n_items, int grid, Status* status, cudaStream_t st) {
+  switch (storage) {
+    case LB_F64: return rows_batch_t<LB_F64>(reps, items, n_items, grid, status, st);
+    case LB_F32: return rows_batch_t<LB_F32>(reps, items, n_items, grid, status, st);
+    case LB_BF16_DEV: return rows_batch_t<LB_BF16_DEV>(reps, items, n_items, grid, status, st);
+    case LB_F16_DEV: return rows_batch_t<LB_F16_DEV>(reps, items, n_items, grid, status, st);
   }
   return cudaErrorInvalidValue;
 }

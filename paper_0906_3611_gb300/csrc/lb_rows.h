@@ -1,14 +1,46 @@
-// lb_rows.h -- launcher of the row-streaming fused step kernel (lb_rows.cu).
+// lb_rows.h -- launchers of the row-streaming fused step kernels (lb_rows.cu).
 #pragma once
 
 #include "lb_kernels.h"
 
 namespace lbk {
 
-// True if the row-streaming kernel handles this lattice and storage.
+// Per-replica record of a batched ensemble, in device memory.
+template <typename C>
+struct ReplicaDev {
+  Geom g;
+  Phys<C> ph;
+  void* buf[2];        // the two population buffers
+  int nitems;          // work items of this replica per step
+  int parity;          // buffer holding the current state
+  long long remaining; // steps left in the budget (<= 0: idle)
+  long long t;         // steps taken since (re)initialisation
+  unsigned int done;   // items finished in the current step
+};
+
+// One work item: strip starting at column x0, output rows [ylo, yhi).
+struct WorkItem {
+  int replica, x0, ylo, yhi;
+};
+
+// Columns per strip of the row-streaming kernels.
+int rows_strip_width();
+
+// True if the row-streaming kernel handles this lattice shape and storage.
+bool rows_geometry_ok(const Geom& g, int storage);
+
+// As rows_geometry_ok, and the kernels can be launched on this device.
 bool rows_supported(const Geom& g, int storage);
+
+// Persistent grid size (resident CTAs) of the batched kernel.
+int rows_batch_grid(int storage);
 
 cudaError_t launch_step_rows(int storage, const void* src, void* dst, const Geom& g,
                              const PhysD& ph, Status* status, cudaStream_t st);
+
+// One step of every replica with budget left; `reps` is a device array of
+// ReplicaDev<float> (FP32 and 16-bit storages) or ReplicaDev<double> (FP64).
+cudaError_t launch_step_rows_batch(int storage, void* reps, const WorkItem* items,
+                                   const int* n_items, int grid, Status* status, cudaStream_t st);
 
 }  // namespace lbk

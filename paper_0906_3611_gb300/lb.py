@@ -26,7 +26,9 @@ ELEM_BYTES = {LB_F64: 8, LB_F32: 4, LB_BF16_DEV: 2, LB_F16_DEV: 2}
 EXPORTED = ["lb_state_bytes", "lb_create", "lb_create_on", "lb_init_random", "lb_step",
             "lb_observables", "lb_get_state", "lb_set_state", "lb_set_state_raw",
             "lb_get_state_raw", "lb_time", "lb_status", "lb_sync", "lb_destroy", "lb_strerror",
-            "lb_observables_noalloc"]
+            "lb_observables_noalloc", "lb_batch_create", "lb_batch_add", "lb_batch_remove",
+            "lb_batch_set_steps", "lb_batch_run", "lb_batch_poll", "lb_batch_observables",
+            "lb_batch_get_state", "lb_batch_autotune", "lb_batch_status", "lb_batch_destroy"]
 
 
 class lb_params(ctypes.Structure):
@@ -70,6 +72,18 @@ def _load():
         "lb_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "lb_observables_noalloc": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, pp,
                                                   vp, vp]),
+        "lb_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, vp, hp]),
+        "lb_batch_add": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, pp, ctypes.c_uint64,
+                                        ctypes.c_int64, ctypes.POINTER(ctypes.c_int)]),
+        "lb_batch_remove": (ctypes.c_int, [vp, ctypes.c_int]),
+        "lb_batch_set_steps": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int64]),
+        "lb_batch_run": (ctypes.c_int, [vp, ctypes.c_int64]),
+        "lb_batch_poll": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+        "lb_batch_observables": (ctypes.c_int, [vp, ctypes.c_int, dp, dp, dp, dp]),
+        "lb_batch_get_state": (ctypes.c_int, [vp, ctypes.c_int, dp]),
+        "lb_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+        "lb_batch_status": (ctypes.c_int, [vp]),
+        "lb_batch_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -187,6 +201,64 @@ def lb_observables_noalloc(f_ptr: int, nx: int, ny: int, pitch: int, params: lb_
            "lb_observables_noalloc")
 
 
+# ---- batched ensembles ----
+
+def lb_batch_create(capacity: int, storage: int, stream: int | None = None) -> int:
+    b = ctypes.c_void_p()
+    _check(_lib.lb_batch_create(capacity, storage, ctypes.c_void_p(stream or 0), ctypes.byref(b)),
+           "lb_batch_create")
+    return b.value
+
+
+def lb_batch_add(b: int, nx: int, ny: int, params: lb_params, seed: int, steps: int) -> int:
+    slot = ctypes.c_int(-1)
+    _check(_lib.lb_batch_add(b, nx, ny, ctypes.byref(params), ctypes.c_uint64(seed), steps,
+                             ctypes.byref(slot)), "lb_batch_add")
+    return slot.value
+
+
+def lb_batch_remove(b: int, slot: int) -> None:
+    _check(_lib.lb_batch_remove(b, slot), "lb_batch_remove")
+
+
+def lb_batch_set_steps(b: int, slot: int, steps: int) -> None:
+    _check(_lib.lb_batch_set_steps(b, slot, steps), "lb_batch_set_steps")
+
+
+def lb_batch_run(b: int, n: int) -> None:
+    _check(_lib.lb_batch_run(b, n), "lb_batch_run")
+
+
+def lb_batch_poll(b: int, capacity: int):
+    rem = (ctypes.c_int64 * capacity)()
+    done = (ctypes.c_int64 * capacity)()
+    _check(_lib.lb_batch_poll(b, rem, done), "lb_batch_poll")
+    return np.array(rem[:]), np.array(done[:])
+
+
+def lb_batch_observables(b: int, slot: int, rho=None, u=None, stress=None, mass=None) -> None:
+    _check(_lib.lb_batch_observables(b, slot, _dp(rho), _dp(u), _dp(stress), _dp(mass)),
+           "lb_batch_observables")
+
+
+def lb_batch_get_state(b: int, slot: int, f: np.ndarray) -> None:
+    _check(_lib.lb_batch_get_state(b, slot, _dp(f)), "lb_batch_get_state")
+
+
+def lb_batch_autotune(b: int, steps_per_candidate: int) -> int:
+    rows = ctypes.c_int(0)
+    _check(_lib.lb_batch_autotune(b, steps_per_candidate, ctypes.byref(rows)), "lb_batch_autotune")
+    return rows.value
+
+
+def lb_batch_status(b: int) -> int:
+    return int(_lib.lb_batch_status(b))
+
+
+def lb_batch_destroy(b: int) -> None:
+    _lib.lb_batch_destroy(b)
+
+
 def lb_strerror(code: int) -> str:
     return _lib.lb_strerror(code).decode()
 
@@ -263,6 +335,73 @@ class Lattice:
             lb_destroy(self.h)
             self.h = None
         self._bufs = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """A batched ensemble of independent lattices (see include/lb.h, lb_batch_*)."""
+
+    def __init__(self, capacity: int, storage: int, stream=None):
+        import torch
+
+        self.capacity = capacity
+        self.storage = storage
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.h = lb_batch_create(capacity, storage, self.stream.cuda_stream)
+        self.shapes = {}
+
+    def add(self, nx: int, ny: int, params: lb_params, seed: int, steps: int) -> int:
+        slot = lb_batch_add(self.h, nx, ny, params, seed, steps)
+        self.shapes[slot] = (nx, ny)
+        return slot
+
+    def remove(self, slot: int):
+        lb_batch_remove(self.h, slot)
+        self.shapes.pop(slot, None)
+
+    def set_steps(self, slot: int, steps: int):
+        lb_batch_set_steps(self.h, slot, steps)
+
+    def run(self, n: int):
+        lb_batch_run(self.h, n)
+        return self
+
+    def poll(self):
+        return lb_batch_poll(self.h, self.capacity)
+
+    def observables(self, slot: int, fields: bool = False) -> dict:
+        nx, ny = self.shapes[slot]
+        stress, mass = np.zeros(3), np.zeros(4)
+        rho = u = None
+        if fields:
+            rho, u = np.zeros((2, ny, nx)), np.zeros((2, ny, nx))
+        lb_batch_observables(self.h, slot, rho, u, stress, mass)
+        out = {"stress": stress, "mass": mass}
+        if fields:
+            out["rho"], out["u"] = rho, u
+        return out
+
+    def get_state(self, slot: int) -> np.ndarray:
+        nx, ny = self.shapes[slot]
+        f = np.empty((2, 9, ny, nx))
+        lb_batch_get_state(self.h, slot, f)
+        return f
+
+    def autotune(self, steps_per_candidate: int = 4) -> int:
+        return lb_batch_autotune(self.h, steps_per_candidate)
+
+    def status(self) -> int:
+        return lb_batch_status(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lb_batch_destroy(self.h)
+            self.h = None
 
     def __del__(self):
         try:
