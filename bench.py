@@ -43,6 +43,11 @@ BATCHES = {
     "batch256_f32": (256, (128, 256, 512, 1024), 0.05, 1),
     "batch256_f16dev": (256, (128, 256, 512, 1024), 0.05, 3),
 }
+SERVES = {
+    # name: (storage, requests, rate per s, sides, steps range, HBM budget, slots, chunk)
+    "serve_f32": (1, 48, 50.0, tuple(range(64, 2049, 64)), (1e3, 1e5), 150e9, 64, 256),
+    "serve_f16dev": (3, 48, 50.0, tuple(range(64, 2049, 64)), (1e3, 1e5), 150e9, 64, 256),
+}
 STORAGE_NAME = {0: "f64", 1: "f32", 2: "bf16dev", 3: "f16dev"}
 ELEM = {0: 8, 1: 4, 2: 2, 3: 2}
 
@@ -367,6 +372,51 @@ def run_batch(args):
         print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """Serving loop: Poisson arrivals of simulation requests, continuous batching."""
+    import numpy as np
+    import torch
+
+    from paper_0906_3611_gb300 import lb, serve
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    storage, n, rate, sides, steps_range, budget, slots, chunk = SERVES[args.workload]
+    if args.requests:
+        n = args.requests
+    reqs = serve.poisson_requests(n, rate=rate, seed=rank, sides=sides, steps_range=steps_range)
+    offered = sum(r.side * r.side * r.steps for r in reqs)
+    srv = serve.Server(PHYS, storage, capacity=slots, chunk=chunk, budget_bytes=budget)
+    sampler = ClockSampler(local)
+    sampler.start()
+    t0 = time.perf_counter()
+    res = srv.run(reqs)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    srv.close()
+    lat = np.array([r.latency for r in res])
+    done_updates = sum(r.side * r.side * r.steps for r in res)
+    value = done_updates / wall / 1e6
+    span = max(r.arrival for r in reqs)
+    if rank == 0:
+        line = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
+                "steps": int(sum(r.steps for r in res)), "warmup": 0,
+                "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": args.workload, "requests": n, "arrival_rate_per_s": rate,
+                           "sides": f"uniform {sides[0]}..{sides[-1]} step 64",
+                           "steps": "log-uniform [1e3, 1e5]", "hbm_budget_gb": budget / 1e9,
+                           "slots": slots, "chunk_steps": chunk, "storage": STORAGE_NAME[storage]},
+                "served": {"completed": len(res), "wall_s": wall,
+                           "latency_p50_s": float(np.percentile(lat, 50)),
+                           "latency_p99_s": float(np.percentile(lat, 99)),
+                           "offered_mlups": offered / max(span, 1e-9) / 1e6,
+                           "overload_factor": (offered / max(span, 1e-9)) / (done_updates / wall)},
+                "clocks": clocks, "impl": "gb300"}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -374,7 +424,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="couette4096_f32",
-                    choices=sorted(WORKLOADS) + sorted(BATCHES))
+                    choices=sorted(WORKLOADS) + sorted(BATCHES) + sorted(SERVES))
+    ap.add_argument("--requests", type=int, default=0)
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -384,6 +435,8 @@ def main():
         run_reference(args)
     elif args.workload in BATCHES:
         run_batch(args)
+    elif args.workload in SERVES:
+        run_serve(args)
     else:
         run_gpu(args)
 

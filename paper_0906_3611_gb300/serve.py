@@ -1,0 +1,170 @@
+"""Continuous-batching server for lattice Boltzmann simulation requests.
+
+A request asks for `steps` steps of one lattice (side x side, its own seed,
+boundary and wall speed).  The server keeps one batched ensemble
+(lb_batch_*) resident on the GPU: requests that arrive while others run are
+admitted into free slots as long as their population buffers fit the HBM
+budget, every chunk of steps advances all admitted requests in one launch
+per step, each request stops on the device when its own step budget is
+spent, and finished requests are reduced (FP64 mass and stress), returned
+and their slots and memory freed before the next chunk.
+
+Scheduling only: every step of every request runs in liblb.so's kernels.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+
+import numpy as np
+
+from . import lb
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    side: int
+    steps: int
+    seed: int
+    boundary: int = lb.LB_PERIODIC
+    U_wall: float = 0.0
+    arrival: float = 0.0  # seconds after the start of the run
+
+
+@dataclasses.dataclass
+class Result:
+    rid: int
+    side: int
+    steps: int
+    arrival: float
+    admitted: float
+    finished: float
+    mass: np.ndarray
+    stress: np.ndarray
+    state: np.ndarray | None = None
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+class Server:
+    """Admission by HBM budget, one resident batch, chunked stepping."""
+
+    def __init__(self, phys: dict, storage: int = lb.LB_F32, capacity: int = 64,
+                 budget_bytes: float = 150e9, chunk: int = 256, rho_ref=(0.88, 0.44),
+                 init_kind: int = lb.LB_INIT_BERNOULLI, init=(0.7, 1.2, 0.1, 0.02),
+                 keep_state: bool = False, stream=None):
+        import torch
+
+        self.phys = phys
+        self.storage = storage
+        self.capacity = capacity
+        self.budget = float(budget_bytes)
+        self.chunk = int(chunk)
+        self.rho_ref = rho_ref
+        self.init_kind = init_kind
+        self.init = init
+        self.keep_state = keep_state
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.batch = lb.Batch(capacity, storage, self.stream)
+        self.queue: collections.deque[Request] = collections.deque()
+        self.active: dict[int, tuple[Request, float]] = {}  # slot -> (request, admitted)
+        self.used = 0.0
+        self.site_updates = 0
+        self.t0 = time.perf_counter()
+
+    def now(self) -> float:
+        return time.perf_counter() - self.t0
+
+    def bytes_of(self, req: Request) -> int:
+        return 2 * lb.lb_state_bytes(req.side, req.side, self.storage)
+
+    def params(self, req: Request) -> lb.lb_params:
+        return lb.make_params(**self.phys, boundary=req.boundary, U_wall=req.U_wall,
+                              storage=self.storage, rho_ref=self.rho_ref,
+                              init_kind=self.init_kind, init=self.init)
+
+    def submit(self, req: Request):
+        if self.bytes_of(req) > self.budget:
+            raise ValueError(f"request {req.rid} needs more than the whole HBM budget")
+        self.queue.append(req)
+
+    def admit(self) -> int:
+        """Move queued requests into free slots while their memory fits (FIFO)."""
+        n = 0
+        while self.queue and len(self.active) < self.capacity:
+            req = self.queue[0]
+            need = self.bytes_of(req)
+            if self.used + need > self.budget:
+                break
+            self.queue.popleft()
+            slot = self.batch.add(req.side, req.side, self.params(req), req.seed, req.steps)
+            self.active[slot] = (req, self.now())
+            self.used += need
+            n += 1
+        return n
+
+    def step_chunk(self) -> list[Result]:
+        """Advance every admitted request by up to `chunk` steps; retire the finished."""
+        if not self.active:
+            return []
+        self.batch.run(self.chunk)
+        remaining, done = self.batch.poll()
+        status = self.batch.status()
+        if status not in (lb.LB_OK, lb.LB_ENEGRHO):
+            raise lb.LBError(status, "batch step")
+        out = []
+        for slot, (req, admitted) in list(self.active.items()):
+            if remaining[slot] > 0:
+                continue
+            obs = self.batch.observables(slot)
+            state = self.batch.get_state(slot) if self.keep_state else None
+            out.append(Result(req.rid, req.side, int(done[slot]), req.arrival, admitted, self.now(),
+                              obs["mass"], obs["stress"], state))
+            self.batch.remove(slot)
+            del self.active[slot]
+            self.used -= self.bytes_of(req)
+            self.site_updates += req.side * req.side * req.steps
+        return out
+
+    def run(self, requests: list[Request], time_limit: float | None = None) -> list[Result]:
+        """Serve requests arriving at their `arrival` times (seconds from now)."""
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        self.t0 = time.perf_counter()
+        results: list[Result] = []
+        while pending or self.queue or self.active:
+            t = self.now()
+            if time_limit is not None and t > time_limit:
+                break
+            while pending and pending[0].arrival <= t:
+                self.submit(pending.popleft())
+            self.admit()
+            if self.active:
+                results.extend(self.step_chunk())
+            elif pending:
+                time.sleep(max(0.0, min(0.01, pending[0].arrival - self.now())))
+        return results
+
+    def close(self):
+        self.batch.close()
+
+
+def poisson_requests(n: int, rate: float, seed: int, sides, steps_range, couette_fraction=0.5,
+                     umax: float = 0.05) -> list[Request]:
+    """n requests with exponential inter-arrival times (mean 1/rate), sides drawn
+    uniformly from `sides`, steps log-uniform in steps_range, periodic or Couette
+    with probability couette_fraction, U uniform in [0, umax]."""
+    g = np.random.Generator(np.random.Philox(key=seed))
+    arrivals = np.cumsum(g.exponential(1.0 / rate, size=n))
+    side = g.choice(np.asarray(sides), size=n)
+    lo, hi = np.log(steps_range[0]), np.log(steps_range[1])
+    steps = np.exp(g.uniform(lo, hi, size=n)).astype(np.int64)
+    couette = g.uniform(size=n) < couette_fraction
+    U = g.uniform(0.0, umax, size=n)
+    return [Request(rid=k, side=int(side[k]), steps=int(steps[k]), seed=1000 + k,
+                    boundary=lb.LB_COUETTE if couette[k] else lb.LB_PERIODIC,
+                    U_wall=float(U[k]) if couette[k] else 0.0, arrival=float(arrivals[k]))
+            for k in range(n)]
