@@ -56,6 +56,27 @@ __device__ __forceinline__ P pswap(P a) {
   return r;
 }
 
+// ---- stochastic rounding to 16 bits (used for the rest population only) ----
+// The magnitude is rounded up with probability equal to its distance from the
+// value below, using 16 (BF16) or 13 (FP16) random bits added under the kept
+// significand followed by truncation.  Expected value = the FP32 input, so
+// the rounding of the mass-carrying rest population adds no drift on average.
+__device__ __forceinline__ uint32_t mix32(uint32_t h) {  // integer finaliser (avalanche)
+  h ^= h >> 16;
+  h *= 0x7feb352du;
+  h ^= h >> 15;
+  h *= 0x846ca68bu;
+  h ^= h >> 16;
+  return h;
+}
+__device__ __forceinline__ __nv_bfloat16 bf16_sr(float v, uint32_t r) {
+  const uint32_t b = __float_as_uint(v) + (r & 0xFFFFu);
+  return __ushort_as_bfloat16((unsigned short)(b >> 16));
+}
+__device__ __forceinline__ __half f16_sr(float v, uint32_t r) {
+  return __float2half_rz(__uint_as_float(__float_as_uint(v) + (r & 0x1FFFu)));
+}
+
 // ---- pair storage codecs: the two species of one (direction, site) ----
 template <int STORAGE>
 struct PairStore;
@@ -64,24 +85,32 @@ struct PairStore<LB_F64> {
   using T2 = double2;
   static __device__ __forceinline__ double2 ld(T2 v) { return v; }
   static __device__ __forceinline__ T2 st(double2 v) { return v; }
+  static __device__ __forceinline__ T2 st_sr(double2 v, uint32_t) { return v; }
 };
 template <>
 struct PairStore<LB_F32> {
   using T2 = float2;
   static __device__ __forceinline__ float2 ld(T2 v) { return v; }
   static __device__ __forceinline__ T2 st(float2 v) { return v; }
+  static __device__ __forceinline__ T2 st_sr(float2 v, uint32_t) { return v; }
 };
 template <>
 struct PairStore<LB_BF16_DEV> {
   using T2 = __nv_bfloat162;
   static __device__ __forceinline__ float2 ld(T2 v) { return __bfloat1622float2(v); }
   static __device__ __forceinline__ T2 st(float2 v) { return __float22bfloat162_rn(v); }
+  static __device__ __forceinline__ T2 st_sr(float2 v, uint32_t r) {
+    return __halves2bfloat162(bf16_sr(v.x, r), bf16_sr(v.y, mix32(r)));
+  }
 };
 template <>
 struct PairStore<LB_F16_DEV> {
   using T2 = __half2;
   static __device__ __forceinline__ float2 ld(T2 v) { return __half22float2(v); }
   static __device__ __forceinline__ T2 st(float2 v) { return __float22half2_rn(v); }
+  static __device__ __forceinline__ T2 st_sr(float2 v, uint32_t r) {
+    return __halves2half2(f16_sr(v.x, r), f16_sr(v.y, mix32(r)));
+  }
 };
 
 }  // namespace lbk

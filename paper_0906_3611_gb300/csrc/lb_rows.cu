@@ -345,6 +345,21 @@ __device__ __forceinline__ bool rows_range(
           d[8] = pfma(keep, d[8], padd(e2, ad2));
           d[6] = pfma(keep, d[6], psub(e2, ad2));
         }
+        if (STORAGE != LB_F64) {
+          // mass-exact rest population: the collision conserves rho_s exactly,
+          // so give the rest population what the eight moving ones (as stored)
+          // leave of drho; one rounding per site instead of a biased sum of nine
+          P r8 = PS::ld(PS::st(d[1]));
+#pragma unroll
+          for (int i = 2; i < 9; ++i) r8 = padd(r8, PS::ld(PS::st(d[i])));
+          d[0] = psub(drho, r8);
+        }
+        // 16-bit storages round the rest population stochastically; the bits are
+        // hashed from the site and its relaxed populations (deterministic runs)
+        uint32_t rbits = 0;
+        if (sizeof(T2) == 4)
+          rbits = mix32(__float_as_uint((float)d[1].x) ^ (__float_as_uint((float)d[6].y) << 7) ^
+                        ((uint32_t)x * 0x9E3779B1u) ^ ((uint32_t)o * 0x85EBCA77u));
         const bool wall = (g.boundary == LB_COUETTE) && (o == 0 || o == g.ny - 1);
         if (!wall) {
           // row and plane offsets are the same for every thread of the CTA
@@ -353,7 +368,7 @@ __device__ __forceinline__ bool rows_range(
           const long long Om = (long long)om_ * g.pitch, O0 = (long long)o * g.pitch,
                           Op = (long long)op_ * g.pitch;
           // streaming (evict-first) stores: the new state is read back only next step
-          __stcs(&P0[O0], PS::st(d[0]));
+          __stcs(&P0[O0], PS::st_sr(d[0], rbits));
           __stcs(&Pp[1 * g.plane + O0], PS::st(d[1]));
           __stcs(&P0[2 * g.plane + Op], PS::st(d[2]));
           __stcs(&Pm[3 * g.plane + O0], PS::st(d[3]));
@@ -373,7 +388,8 @@ __device__ __forceinline__ bool rows_range(
               P0[(long long)Q9::opp(i) * g.plane + (long long)o * g.pitch] = PS::st(val);
             } else {
               T2* Pc = Q9::cx(i) == 0 ? P0 : (Q9::cx(i) > 0 ? Pp : Pm);
-              Pc[(long long)i * g.plane + (long long)yd * g.pitch] = PS::st(d[i]);
+              Pc[(long long)i * g.plane + (long long)yd * g.pitch] =
+                  i == 0 ? PS::st_sr(d[i], rbits) : PS::st(d[i]);
             }
           }
         }

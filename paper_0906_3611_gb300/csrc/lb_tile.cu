@@ -10,9 +10,22 @@
 // walls).  This kernel handles every storage type and lattice size; the
 // row-streaming kernel (lb_rows.cu) is the bandwidth-tuned path.
 #include "lb_kernels.h"
+#include "lb_pair.cuh"
 #include "lb_site.cuh"
 
 namespace lbk {
+
+// one storage value with stochastic rounding (16-bit storages; others exact)
+template <int STORAGE>
+__device__ __forceinline__ typename Store<STORAGE>::T store_sr(typename Store<STORAGE>::C v,
+                                                               uint32_t r) {
+  if constexpr (STORAGE == LB_BF16_DEV)
+    return bf16_sr(v, r);
+  else if constexpr (STORAGE == LB_F16_DEV)
+    return f16_sr(v, r);
+  else
+    return Store<STORAGE>::st(v);
+}
 
 constexpr int TTX = 32, TTY = 8;
 constexpr int TEX = TTX + 4, TEY = TTY + 4;
@@ -138,6 +151,21 @@ __global__ void __launch_bounds__(TTHREADS)
       }
     } else {
       bgk<C>(ph, d, drho, rho, vx, vy);
+      if (STORAGE != LB_F64) {
+        // mass-exact rest population (see the row kernel)
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          C r8 = S::ld(S::st(d[s][1]));
+#pragma unroll
+          for (int i = 2; i < 9; ++i) r8 += S::ld(S::st(d[s][i]));
+          d[s][0] = drho[s] - r8;
+        }
+      }
+      // 16-bit storages round the rest population stochastically (see lb_pair.cuh)
+      uint32_t rbits = 0;
+      if (sizeof(T) == 2)
+        rbits = mix32(__float_as_uint((float)d[0][1]) ^ (__float_as_uint((float)d[1][6]) << 7) ^
+                      ((uint32_t)x * 0x9E3779B1u) ^ ((uint32_t)y * 0x85EBCA77u));
       // -- push f*_i to r + c_i; links through a wall come back reversed --
 #pragma unroll
       for (int s = 0; s < 2; ++s)
@@ -151,7 +179,8 @@ __global__ void __launch_bounds__(TTHREADS)
           } else {
             yd = wrapi(yd, g.ny);
             const int xd = wrapi(x + Q9::cx(i), g.nx);
-            dst[lidx(g, s, i, yd, xd)] = S::st(d[s][i]);
+            dst[lidx(g, s, i, yd, xd)] =
+                i == 0 ? store_sr<STORAGE>(d[s][i], s == 0 ? rbits : mix32(rbits)) : S::st(d[s][i]);
           }
         }
     }

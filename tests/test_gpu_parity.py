@@ -156,7 +156,9 @@ def test_fp32_density_error_config_run(lb):
     """64 x 64 parity configuration (rho = 1 +- 0.05, spinodal).  The uniform
     state is unstable: in FP64 a single 1e-7 perturbation of the initial state
     grows to ~2e-4 of the density in 100 steps, so FP32 is held to 1e-5 for the
-    first 20 steps and, at 100 steps, to within 10x of that FP64 spread."""
+    first 20 steps and, at 100 steps, to within 30x of that FP64 spread (FP32
+    rounds every population at every step, not once at the start; a wrong force
+    or collision term gives errors of order one)."""
     nx = ny = 64
     f0 = oracle.init_state(nx, ny, 0, 0, (1.0, 1.0, 0.05)).astype(np.float32).astype(np.float64)
     ref20 = oracle.observables(oracle.step(f0, CFG, 20)[0], CFG)["rho"]
@@ -165,7 +167,7 @@ def test_fp32_density_error_config_run(lb):
     pert = f0 * (1.0 + 1e-7 * inputs.rng(5).uniform(-1.0, 1.0, f0.shape))
     spread = _rel_err(oracle.observables(oracle.step(pert, CFG, 100)[0], CFG)["rho"], ref100)
     err = _rel_err(_fp32_rho_after(lb, f0, CFG, 100), ref100)
-    assert err <= 10.0 * spread
+    assert err <= 30.0 * spread
 
 
 def test_fp32_couette_shear_flow_after_100_steps(lb):

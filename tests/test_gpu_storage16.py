@@ -6,10 +6,15 @@ Stated bounds (measured on GB300, then given a ~3x margin):
   <= 1e-3 (BF16, 8-bit significand) and <= 1e-4 (FP16, 11-bit), both step
   kernels, both boundary kinds;
 * per-species mass drift of the 512 x 512 Bernoulli droplet emulsion after
-  1000 steps (rho_ref = the species means): FP32 <= 5e-5, FP16 <= 3e-3,
-  BF16 <= 0.1.  Rounding the deviations breaks exact mass conservation; in a
-  droplet mixture the deviations are as large as the densities themselves,
-  so BF16 storage drifts by percents and is meant for near-uniform states.
+  1000 steps (rho_ref = the species means): FP32 <= 1e-6, FP16 <= 2e-4,
+  BF16 <= 5e-4 (measured 1e-8, 2e-5, 5e-5: ~10x margin, the 16-bit drift
+  being a random walk).  The collision conserves rho_s, so the kernels give
+  the rest population what the eight stored moving populations leave of the
+  site's density, and the 16-bit storages round that one population
+  stochastically: the only mass error left is the zero-mean rounding of the
+  rest population.  Round-to-nearest there drifted by 2.5e-3 (FP16) and 3e-2
+  (BF16) in 1000 steps, because the bulk sites of a droplet all round the
+  same value the same way.
 """
 import numpy as np
 import pytest
@@ -54,7 +59,7 @@ def test_one_step_near_reference_state(lb, monkeypatch, kernel, boundary, U, sto
     assert _rel(g, ref) <= tol
 
 
-@pytest.mark.parametrize("storage,bound", [("f32", 5e-5), ("f16", 3e-3), ("bf16", 0.1)])
+@pytest.mark.parametrize("storage,bound", [("f32", 1e-6), ("f16", 2e-4), ("bf16", 5e-4)])
 def test_mass_drift_of_the_droplet_emulsion(lb, storage, bound):
     st = {"f32": lb.LB_F32, "f16": lb.LB_F16_DEV, "bf16": lb.LB_BF16_DEV}[storage]
     p = lb.make_params(**CFG, storage=st, rho_ref=(0.88, 0.44), init_kind=lb.LB_INIT_BERNOULLI,
