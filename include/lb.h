@@ -67,11 +67,18 @@ extern "C" {
                          mirrored about each wall                           */
 
 /* ---- population storage in device memory (arithmetic: FP64 for LB_F64,
- *      FP32 otherwise) ---- */
-#define LB_F64 0      /* double                                              */
-#define LB_F32 1      /* float                                               */
-#define LB_BF16_DEV 2 /* bfloat16 deviation f_i - w_i rho_ref,s (RN-even)    */
-#define LB_F16_DEV 3  /* IEEE half deviation f_i - w_i rho_ref,s (RN-even)   */
+ *      FP32 otherwise).  Every storage but LB_F64 holds the deviation
+ *      d_i = f_i - w_i rho_ref,s, so that rounding errors scale with |d_i|
+ *      (rho_ref = 0 stores plain populations).  The collision conserves
+ *      rho_s, so the rest population is stored as what the eight moving
+ *      ones, as stored, leave of the site's density deviation; the 16-bit
+ *      storages round that one value stochastically (bits hashed from the
+ *      site and its populations: runs are deterministic) and every other
+ *      value to nearest-even. ---- */
+#define LB_F64 0      /* double populations f_i                              */
+#define LB_F32 1      /* float deviation f_i - w_i rho_ref,s                 */
+#define LB_BF16_DEV 2 /* bfloat16 deviation f_i - w_i rho_ref,s             */
+#define LB_F16_DEV 3  /* IEEE half deviation f_i - w_i rho_ref,s            */
 
 /* ---- seeded initial densities (lb_init_random) ---- */
 #define LB_INIT_UNIFORM_NOISE 0 /* rho_A = init[0] + init[2] (2u1 - 1),
@@ -92,8 +99,10 @@ typedef struct {
   int boundary;      /* LB_PERIODIC or LB_COUETTE                               */
   double U_wall;     /* wall speed U for LB_COUETTE (lattice units)            */
   int storage;       /* LB_F64, LB_F32, LB_BF16_DEV or LB_F16_DEV               */
-  double rho_ref[2]; /* reference densities of the *_DEV storages (ignored
-                        otherwise); exp(-rho_ref/rho0) is taken in FP64       */
+  double rho_ref[2]; /* reference densities of the deviation storages (all
+                        but LB_F64, where they are ignored); the species mean
+                        densities are a good choice; exp(-rho_ref/rho0) is
+                        taken in FP64                                        */
   int init_kind;     /* LB_INIT_UNIFORM_NOISE or LB_INIT_BERNOULLI              */
   double init[6];    /* recipe parameters, see the LB_INIT_* kinds             */
 } lb_params;
@@ -152,7 +161,8 @@ LB_API int lb_set_state(lb_handle *h, const double *f);
 
 /* Native-format state exchange, no conversion: the device's own element order
  * without row padding, f[i][y][x][s] (direction, row, column, species) in the
- * storage type (8, 4 or 2 bytes per element), 9*ny*nx*2 elements.
+ * storage type (8, 4 or 2 bytes per element), 9*ny*nx*2 elements, holding
+ * what the storage holds (deviations for all but LB_F64).
  * lb_set_state_raw copies from host memory (pinned memory makes it a DMA at
  * full link speed) and returns after enqueueing (asynchronous, like
  * cudaMemcpyAsync: the host buffer must stay valid until the stream reaches

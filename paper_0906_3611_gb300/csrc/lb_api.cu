@@ -65,20 +65,8 @@ static int validate(int nx, int ny, const lb_params* p) {
 
 static void fill_phys(lb_handle* h) {
   const lb_params& p = h->p;
-  PhysD& d = h->ph;
-  const bool dev = (p.storage == LB_BF16_DEV || p.storage == LB_F16_DEV);
-  d.dev = dev ? 1 : 0;
-  for (int s = 0; s < 2; ++s) {
-    d.tau[s] = p.tau[s];
-    d.omega[s] = 1.0 / p.tau[s];
-    d.Ga[s] = p.Ga[s];
-    d.Gr[s] = p.Gr[s];
-    d.rho_ref[s] = dev ? p.rho_ref[s] : 0.0;
-    d.E[s] = exp(-d.rho_ref[s] / p.rho0);  // FP64 exponential of the reference shift
-  }
-  d.rho0 = p.rho0;
-  d.G_AB = p.G_AB;
-  d.U = (p.boundary == LB_COUETTE) ? p.U_wall : 0.0;
+  h->ph = physd_from_params(p.storage, p.tau, p.rho0, p.G_AB, p.Ga, p.Gr, p.boundary, p.U_wall,
+                            p.rho_ref);
 }
 
 static int create_common(int nx, int ny, const lb_params* p, void* stream, void* b0, void* b1,

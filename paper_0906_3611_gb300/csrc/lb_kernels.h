@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include "lb_common.cuh"
@@ -12,8 +13,33 @@ namespace lbk {
 // Physics constants in FP64, as prepared by the API layer from lb_params.
 struct PhysD {
   double tau[2], omega[2], rho0, G_AB, Ga[2], Gr[2], U, rho_ref[2], E[2];
-  int dev;  // 1 for the deviation (16-bit) storages
+  int dev;  // 1 for the deviation storages (every storage but FP64)
 };
+
+// Every storage but FP64 holds deviations d_i = f_i - w_i rho_ref,s: rounding
+// errors then scale with |d_i| instead of |f_i| (FP32 with rho_ref = 0 stores
+// plain populations).  FP64 stores plain populations.
+inline PhysD physd_from_params(int storage, const double tau[2], double rho0, double G_AB,
+                               const double Ga[2], const double Gr[2], int boundary,
+                               double U_wall, const double rho_ref[2]) {
+  PhysD d;
+  const bool dev = (storage != LB_F64);
+  d.dev = dev ? 1 : 0;
+  for (int s = 0; s < 2; ++s) {
+    d.tau[s] = tau[s];
+    d.omega[s] = 1.0 / tau[s];
+    d.Ga[s] = Ga[s];
+    d.Gr[s] = Gr[s];
+    // rounded to FP32, the precision the kernels hold it in, so that the host
+    // (state exchange, initial state) and the device agree on f_i = w_i rho_ref + d_i
+    d.rho_ref[s] = dev ? (double)(float)rho_ref[s] : 0.0;
+    d.E[s] = exp(-d.rho_ref[s] / rho0);  // FP64 exponential of the reference shift
+  }
+  d.rho0 = rho0;
+  d.G_AB = G_AB;
+  d.U = (boundary == LB_COUETTE) ? U_wall : 0.0;
+  return d;
+}
 
 // Number of FP64 observables accumulated per block by the observe kernels:
 // {sum rho_A, sum rho_B, P_x, P_y, sum sigma_xy, wall_top, wall_bottom, 0}.

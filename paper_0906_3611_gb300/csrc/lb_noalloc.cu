@@ -116,8 +116,8 @@ __global__ void __launch_bounds__(NA_THREADS)
     momenta<C>(d, jx, jy);
     C vx[2], vy[2];
     shifted_velocities<C>(ph, rho, jx, jy, Fx, Fy, vx, vy, bad);
-    acc[0] = (double)rho[0];
-    acc[1] = (double)rho[1];
+    acc[0] = (double)ph.rho_ref[0] + (double)drho[0];
+    acc[1] = (double)ph.rho_ref[1] + (double)drho[1];
     acc[2] = (double)jx[0] + (double)jx[1];
     acc[3] = (double)jy[0] + (double)jy[1];
 #pragma unroll
@@ -253,20 +253,8 @@ extern "C" int lb_observables_noalloc(const void* f, int nx, int ny, int pitch, 
   g.pitch = pitch;
   g.boundary = p->boundary;
   g.plane = (long long)ny * pitch;
-  PhysD d;
-  const bool dev = (p->storage == LB_BF16_DEV || p->storage == LB_F16_DEV);
-  d.dev = dev ? 1 : 0;
-  for (int s = 0; s < 2; ++s) {
-    d.tau[s] = p->tau[s];
-    d.omega[s] = 1.0 / p->tau[s];
-    d.Ga[s] = p->Ga[s];
-    d.Gr[s] = p->Gr[s];
-    d.rho_ref[s] = dev ? p->rho_ref[s] : 0.0;
-    d.E[s] = exp(-d.rho_ref[s] / p->rho0);
-  }
-  d.rho0 = p->rho0;
-  d.G_AB = p->G_AB;
-  d.U = (p->boundary == LB_COUETTE) ? p->U_wall : 0.0;
+  const PhysD d = physd_from_params(p->storage, p->tau, p->rho0, p->G_AB, p->Ga, p->Gr,
+                                    p->boundary, p->U_wall, p->rho_ref);
 
   // the status counter must start at zero; every partial record is overwritten
   if (cudaMemsetAsync(scratch + kStatusSlot, 0, sizeof(double), st) != cudaSuccess) return LB_ECUDA;

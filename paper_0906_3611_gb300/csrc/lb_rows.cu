@@ -216,9 +216,11 @@ __device__ __forceinline__ bool rows_range(
   for (int k = 0; k < 5; ++k) Sx[k] = Sy[k] = pbc(C(0));
 #pragma unroll
   for (int k = 0; k < 4; ++k) Cx[k] = Cy[k] = pbc(C(0));
-  P lag_rho[3], lag_psi[3];
+  // density deviations drho_s = sum_i d_i (kept as summed: rho_ref + drho
+  // rounds away the low bits that the mass-exact rest population needs)
+  P lag_drho[3], lag_psi[3];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) lag_rho[k] = lag_psi[k] = pbc(C(0));
+  for (int k = 0; k < 3; ++k) lag_drho[k] = lag_psi[k] = pbc(C(0));
 
   int q = 0;
   int slot = ring % NSLOT, parity = (ring / NSLOT) & 1;  // slot of row q and its phase parity
@@ -232,12 +234,13 @@ __device__ __forceinline__ bool rows_range(
     const T2* srow = stage + slot * SLOT;
     P* rbuf = rowbuf0 + (q & 1) * 2 * EXT;  // [0, EXT): rho pairs; [EXT, 2 EXT): psi pairs
     // ---- density and pseudo-potential pair of this thread's column ----
-    P my_rho = pbc(C(0)), my_psi = pbc(C(0));
+    P my_rho = pbc(C(0)), my_psi = pbc(C(0)), my_drho = pbc(C(0));
     if (ecol >= 0) {
       const T2* p = srow + (ecol - 2 + SOFF);
       P a = PS::ld(p[0]);
 #pragma unroll
       for (int i = 1; i < 9; ++i) a = padd(a, PS::ld(p[i * SW]));
+      my_drho = a;
       my_rho = padd(rho_ref, a);
       const P ex = pmk(exp_c<C>(-a.x * ph.inv_rho0), exp_c<C>(-a.y * ph.inv_rho0));
       my_psi = pfma(mrho0E, ex, pbc(ph.rho0));
@@ -289,7 +292,7 @@ __device__ __forceinline__ bool rows_range(
         Cx[3] = X1;
         Cy[1] = padd(Cy[1], K);
         Cy[3] = psub(pbc(C(0)), K);
-        lag_rho[2] = my_rho;
+        lag_drho[2] = my_drho;
         lag_psi[2] = my_psi;
       }
 
@@ -301,8 +304,8 @@ __device__ __forceinline__ bool rows_range(
         P d[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) d[i] = PS::ld(orow[i * SW]);
-        const P rho = lag_rho[0];
-        const P drho = psub(rho, rho_ref);
+        const P drho = lag_drho[0];
+        const P rho = padd(rho_ref, drho);
         // G = -F: F_s = -psi_s S_s - rho_s C_s
         const P Gx = pfma(lag_psi[0], Sx[0], pmul(rho, Cx[0]));
         const P Gy = pfma(lag_psi[0], Sy[0], pmul(rho, Cy[0]));
@@ -378,14 +381,27 @@ __device__ __forceinline__ bool rows_range(
           __stcs(&Pm[7 * g.plane + Om], PS::st(d[7]));
           __stcs(&Pp[8 * g.plane + Om], PS::st(d[8]));
         } else {
+          // Ladd: a link through the wall comes back along opp(i) at the same
+          // site, less 2 w_i rho_s (c_i . U_w)/cs2 per species
+#pragma unroll
+          for (int i = 1; i < 9; ++i) {
+            const int yd = o + Q9::cy(i);
+            if (yd < 0 || yd >= g.ny) {
+              const C Uw = (yd >= g.ny) ? ph.Uwall : -ph.Uwall;
+              d[i] = pfma(pbc(-C(6) * wq<C>(i) * C(Q9::cx(i)) * Uw), rho, d[i]);
+            }
+          }
+          if (STORAGE != LB_F64) {  // mass-exact again, with the values the wall sends back
+            P r8 = PS::ld(PS::st(d[1]));
+#pragma unroll
+            for (int i = 2; i < 9; ++i) r8 = padd(r8, PS::ld(PS::st(d[i])));
+            d[0] = psub(drho, r8);
+          }
 #pragma unroll
           for (int i = 0; i < 9; ++i) {
             const int yd = o + Q9::cy(i);
             if (yd < 0 || yd >= g.ny) {
-              // Ladd: back along opp(i), less 2 w_i rho_s (c_i . U_w)/cs2 per species
-              const C Uw = (yd >= g.ny) ? ph.Uwall : -ph.Uwall;
-              const P val = pfma(pbc(-C(6) * wq<C>(i) * C(Q9::cx(i)) * Uw), rho, d[i]);
-              P0[(long long)Q9::opp(i) * g.plane + (long long)o * g.pitch] = PS::st(val);
+              P0[(long long)Q9::opp(i) * g.plane + (long long)o * g.pitch] = PS::st(d[i]);
             } else {
               T2* Pc = Q9::cx(i) == 0 ? P0 : (Q9::cx(i) > 0 ? Pp : Pm);
               Pc[(long long)i * g.plane + (long long)yd * g.pitch] =
@@ -405,8 +421,8 @@ __device__ __forceinline__ bool rows_range(
         Cx[k] = Cx[k + 1];
         Cy[k] = Cy[k + 1];
       }
-      lag_rho[0] = lag_rho[1];
-      lag_rho[1] = lag_rho[2];
+      lag_drho[0] = lag_drho[1];
+      lag_drho[1] = lag_drho[2];
       lag_psi[0] = lag_psi[1];
       lag_psi[1] = lag_psi[2];
     }

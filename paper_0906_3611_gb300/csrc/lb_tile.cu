@@ -117,8 +117,10 @@ __global__ void __launch_bounds__(TTHREADS)
     shifted_velocities<C>(ph, rho, jx, jy, Fx, Fy, vx, vy, bad);
 
     if (OBSERVE) {
-      acc[0] = (double)rho[0];
-      acc[1] = (double)rho[1];
+      // densities in FP64 from the reference and the summed deviation (the
+      // FP32 sum rho_ref + drho would round away the low bits of drho)
+      acc[0] = (double)ph.rho_ref[0] + (double)drho[0];
+      acc[1] = (double)ph.rho_ref[1] + (double)drho[1];
       acc[2] = (double)jx[0] + (double)jx[1];
       acc[3] = (double)jy[0] + (double)jy[1];
 #pragma unroll
@@ -151,8 +153,21 @@ __global__ void __launch_bounds__(TTHREADS)
       }
     } else {
       bgk<C>(ph, d, drho, rho, vx, vy);
+      // Ladd: a link through a wall comes back along opp(i) at the same site,
+      // less 2 w_i rho_s (c_i . U_w)/cs2
+      if (g.boundary == LB_COUETTE && (y == 0 || y == g.ny - 1)) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+          for (int i = 1; i < 9; ++i) {
+            const int yd = y + Q9::cy(i);
+            if (yd < 0 || yd >= g.ny)
+              d[s][i] -= wall_term<C>(i, rho[s], (yd >= g.ny) ? ph.Uwall : -ph.Uwall);
+          }
+      }
       if (STORAGE != LB_F64) {
-        // mass-exact rest population (see the row kernel)
+        // mass-exact rest population (see the row kernel), with the values
+        // the walls send back
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
           C r8 = S::ld(S::st(d[s][1]));
@@ -173,9 +188,7 @@ __global__ void __launch_bounds__(TTHREADS)
         for (int i = 0; i < 9; ++i) {
           int yd = y + Q9::cy(i);
           if (g.boundary == LB_COUETTE && (yd < 0 || yd >= g.ny)) {
-            const C Uw = (yd >= g.ny) ? ph.Uwall : -ph.Uwall;
-            const C val = d[s][i] - wall_term<C>(i, rho[s], Uw);
-            dst[lidx(g, s, Q9::opp(i), y, x)] = S::st(val);
+            dst[lidx(g, s, Q9::opp(i), y, x)] = S::st(d[s][i]);
           } else {
             yd = wrapi(yd, g.ny);
             const int xd = wrapi(x + Q9::cx(i), g.nx);
@@ -248,19 +261,20 @@ __global__ void __launch_bounds__(256)
     for (int s = 0; s < 2; ++s)
 #pragma unroll
       for (int i = 0; i < 9; ++i) d[s][i] = S::ld(src[lidx(g, s, i, y, x)]);
-    C rho[2];
+    C rho[2], drho[2];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       C a = C(0);
 #pragma unroll
       for (int i = 0; i < 9; ++i) a += d[s][i];
+      drho[s] = a;
       rho[s] = ph.rho_ref[s] + a;
     }
     C jx[2], jy[2];
     momenta<C>(d, jx, jy);
     const C den = rho[0] * ph.omega[0] + rho[1] * ph.omega[1];
-    out[site] = (double)rho[0];
-    out[n + site] = (double)rho[1];
+    out[site] = (double)ph.rho_ref[0] + (double)drho[0];
+    out[n + site] = (double)ph.rho_ref[1] + (double)drho[1];
     out[2 * n + site] = (double)((jx[0] * ph.omega[0] + jx[1] * ph.omega[1]) / den);
     out[3 * n + site] = (double)((jy[0] * ph.omega[0] + jy[1] * ph.omega[1]) / den);
   }

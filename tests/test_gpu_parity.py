@@ -126,9 +126,9 @@ def test_fp64_free_run_conserves_mass(lb):
     assert np.max(np.abs(m1[2:])) < 1e-10
 
 
-def _fp32_rho_after(lb, f0, phys, steps, boundary=0, U=0.0):
+def _fp32_rho_after(lb, f0, phys, steps, boundary=0, U=0.0, rho_ref=(1.0, 1.0)):
     ny, nx = f0.shape[2:]
-    lat = lb.Lattice(nx, ny, _params(lb, phys, lb.LB_F32, boundary, U))
+    lat = lb.Lattice(nx, ny, _params(lb, phys, lb.LB_F32, boundary, U, rho_ref=rho_ref))
     lat.set_state(f0).step(steps)
     rho = lat.observables(fields=True)["rho"]
     assert lat.status() == lb.LB_OK
@@ -139,7 +139,9 @@ def _fp32_rho_after(lb, f0, phys, steps, boundary=0, U=0.0):
 def test_fp32_density_error_on_a_stable_state_after_100_steps(lb):
     """FP32 storage and arithmetic: max relative density error <= 1e-5 after 100
     steps, from a relaxed flat interface of the rho0 = 0.7 couplings (a stable
-    state, so rounding errors are not amplified)."""
+    state, so rounding errors are not amplified).  The deviations are taken
+    from the species means (0.61): a reference far from both phases (1.0 for
+    the 0.12 phase) costs the dilute phase ~3 bits and gave 2.5e-5."""
     nx, ny = 64, 16
     x = np.arange(nx)
     rA = np.where((x >= 16) & (x < 48), 1.1, 0.12)
@@ -147,7 +149,7 @@ def test_fp32_density_error_on_a_stable_state_after_100_steps(lb):
     f = rho[:, None] * W9[None, :, None, None]
     f, _ = oracle.step(f, CFG, 3000)
     f0 = f.astype(np.float32).astype(np.float64)
-    rho_gpu = _fp32_rho_after(lb, f0, CFG, 100)
+    rho_gpu = _fp32_rho_after(lb, f0, CFG, 100, rho_ref=(0.61, 0.61))
     ref = oracle.observables(oracle.step(f0, CFG, 100)[0], CFG)["rho"]
     assert _rel_err(rho_gpu, ref) <= 1e-5
 
@@ -225,8 +227,10 @@ def test_negative_density_is_flagged_like_the_oracle(lb):
     assert np.allclose(g, ref, rtol=1e-12, atol=1e-15)
 
 
-def _patch_reference(rho0f, ys, xs, ny, nx, phys, boundary, U, dtype):
-    """One oracle step on a local patch around (ys, xs); returns the centre site's f."""
+def _patch_reference(rho0f, ys, xs, ny, nx, phys, boundary, U, dtype, rho_ref=(0.0, 0.0)):
+    """One oracle step on a local patch around (ys, xs); returns the centre site's f.
+    The initial populations are w_i rho_ref,s + (w_i rho_s - w_i rho_ref,s) rounded
+    to `dtype`, as the deviation storages hold them."""
     R = 5
     if boundary == 1 and ys < R:
         rows = np.arange(0, 2 * R + 1)
@@ -236,7 +240,8 @@ def _patch_reference(rho0f, ys, xs, ny, nx, phys, boundary, U, dtype):
         rows = (np.arange(ys - R, ys + R + 1)) % ny
     cols = (np.arange(xs - R, xs + R + 1)) % nx
     rho = rho0f[:, rows][:, :, cols]
-    f = (W9[None, :, None, None] * rho[:, None]).astype(dtype).astype(np.float64)
+    base = W9[None, :, None, None] * np.asarray(rho_ref, dtype=np.float64)[:, None, None, None]
+    f = base + (W9[None, :, None, None] * rho[:, None] - base).astype(dtype).astype(np.float64)
     pb = boundary if (boundary == 1 and (ys < R or ys > ny - 1 - R)) else 0
     g, _ = oracle.step(f, _oracle_p(phys, pb, U), 1)
     cy = int(np.where(rows == ys)[0][0])
@@ -249,18 +254,21 @@ def test_full_size_sampled_sites_fp32_couette(lb):
     nx = ny = 4096
     U = 0.02
     init = (0.7, 1.2, 0.1, 0.02)
-    lat = lb.Lattice(nx, ny, _params(lb, CFG, lb.LB_F32, boundary=1, U=U, kind=1, init=init))
+    rho_ref = np.float32([0.87, 0.43]).astype(np.float64)  # the values the library holds
+    lat = lb.Lattice(nx, ny, _params(lb, CFG, lb.LB_F32, boundary=1, U=U, kind=1, init=init,
+                                     rho_ref=(0.87, 0.43)))
     lat.init_random(0).step(1)
     raw = torch.empty((9, ny, nx, 2), dtype=torch.float32).pin_memory()  # native order [i][y][x][s]
     lb.lb_get_state_raw(lat.h, raw.data_ptr())
     assert lat.status() == lb.LB_OK
     lat.close()
-    got = raw.numpy().transpose(3, 0, 1, 2)
+    got = raw.numpy().transpose(3, 0, 1, 2)  # deviations d_i = f_i - w_i rho_ref,s
+    base = W9[None, :] * rho_ref[:, None]
     rho0f = oracle.init_densities(nx, ny, 0, 1, init)
     sites = inputs.sample_sites(nx, ny, 40, seed=1) + [(0, 17), (1, 900), (ny - 2, 5), (ny - 1, 2048)]
     for (ys, xs) in sites:
-        ref = _patch_reference(rho0f, ys, xs, ny, nx, CFG, 1, U, np.float32)
-        assert _rel_err(got[:, :, ys, xs].astype(np.float64), ref) <= 1e-5, (ys, xs)
+        ref = _patch_reference(rho0f, ys, xs, ny, nx, CFG, 1, U, np.float32, rho_ref)
+        assert _rel_err(base + got[:, :, ys, xs].astype(np.float64), ref) <= 1e-5, (ys, xs)
 
 
 @pytest.mark.parametrize("boundary,U", [(0, 0.0), (1, 0.03)])
