@@ -37,6 +37,8 @@ WORKLOADS = {
     "couette2048_f32": (2048, 2048, 1, 0.02, 1),
     "couette4096_bf16dev": (4096, 4096, 1, 0.02, 2),
     "couette4096_f16dev": (4096, 4096, 1, 0.02, 3),
+    "couette2048_bf16dev": (2048, 2048, 1, 0.02, 2),
+    "couette2048_f16dev": (2048, 2048, 1, 0.02, 3),
 }
 BATCHES = {
     # name: (replicas, side choices, U range, storage)

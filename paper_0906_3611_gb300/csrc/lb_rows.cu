@@ -146,37 +146,95 @@ __device__ __forceinline__ void issue_row(const typename PairStore<STORAGE>::T2*
   }
 }
 
-// One CTA, one work range: columns x0 .. x0+RX-1 (clipped to nx), output rows
-// ylo .. yhi-1 of the lattice (src -> dst).  `ring` is the position of the
-// next staged row in the CTA's slot ring (identical in every thread); on
-// entry every slot is free.  Returns false if a bounded wait gave up (after
-// draining the copies this range issued).
+// The per-thread state of one work range.  The stencil accumulators and the
+// lagged rho/psi rows are windows over rows r-2 .. r+2 of the row r staged in
+// the current iteration; logical index k of a window lives in register slot
+// (k + R) % 5, R = (iteration) % 5, and the row loop is unrolled five times,
+// so that the windows slide by renaming registers instead of moving them.
 template <int STORAGE>
-__device__ __forceinline__ bool rows_range(
-    const typename PairStore<STORAGE>::T2* __restrict__ src,
-    typename PairStore<STORAGE>::T2* __restrict__ dst, const Geom& g,
-    const Phys<typename Store<STORAGE>::C>& ph, int x0, int ylo, int yhi,
-    typename PairStore<STORAGE>::T2* stage, typename PairOf<typename Store<STORAGE>::C>::P* rowbuf0,
-    uint64_t* bars, int& ring, int* s_abort, Status* status, int& bad) {
+struct RowsLoop {
   using PS = PairStore<STORAGE>;
   using T2 = typename PS::T2;
   using C = typename Store<STORAGE>::C;
   using P = typename PairOf<C>::P;
-  constexpr int SOFF = RowsCfg<STORAGE>::SOFF;
-  constexpr int NSLOT = RowsCfg<STORAGE>::NSLOT;
-  constexpr int SW = stage_width<STORAGE>();
-  constexpr int SLOT = 9 * SW;
-  constexpr int EXT = RX + 4;
+  static constexpr int SOFF = RowsCfg<STORAGE>::SOFF;
+  static constexpr int NSLOT = RowsCfg<STORAGE>::NSLOT;
+  static constexpr int SW = stage_width<STORAGE>();
+  static constexpr int SLOT = 9 * SW;
+  static constexpr int EXT = RX + 4;
 
-  const int tid = threadIdx.x;
-  const int warp = tid >> 5, lane = tid & 31;
-  const int nstage = (yhi - ylo) + 4;  // rho rows ylo-2 .. yhi+1
+  const T2* __restrict__ src;
+  const Geom& g;
+  const Phys<C>& ph;
+  T2* stage;
+  P* rowbuf0;
+  uint64_t* bars;
+  int* s_abort;
+  Status* status;
+  int x0, ylo, nstage, ring;
+  // this thread
+  int lane, t, x, ecol, plane;
+  bool producer, compute, active;
+  T2 *Pm, *P0, *Pp;
+  // per-species constants as pairs
+  P Wa, Wb, Wc, Wd, We, W2c, W2d, W2e, rho_ref, mrho0E, om;
+  // windows (see above) and loop state
+  P Sx[5], Sy[5], Cx[5], Cy[5], lag_drho[5], lag_psi[5];
+  int q, slot, parity, issued, bad;
 
-  // the last warp stages rows; a row's slot is refilled once every thread has
+  __device__ __forceinline__ RowsLoop(const T2* __restrict__ src_, T2* __restrict__ dst,
+                                      const Geom& g_, const Phys<C>& ph_, int x0_, int ylo_,
+                                      int yhi, T2* stage_, P* rowbuf0_, uint64_t* bars_,
+                                      int ring_, int* s_abort_, Status* status_)
+      : src(src_), g(g_), ph(ph_), stage(stage_), rowbuf0(rowbuf0_), bars(bars_),
+        s_abort(s_abort_), status(status_), x0(x0_), ylo(ylo_), nstage((yhi - ylo_) + 4),
+        ring(ring_) {
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    lane = tid & 31;
+    producer = (warp == NCW);
+    compute = warp < NCW;
+    t = compute ? tid : 0;
+    x = x0 + t;
+    active = compute && (x < g.nx);
+    // rho/psi column in the ext row [0, RX+4): column x0 - 2 + ecol; the copy
+    // warp's lanes 0..3 form the four halo columns
+    if (compute)
+      ecol = t + 2;
+    else
+      ecol = (lane < 2) ? lane : (lane < 4 ? RX + lane : -1);
+    const int xm = (x == 0) ? g.nx - 1 : x - 1;
+    const int xp = (x >= g.nx - 1) ? 0 : x + 1;
+    // push targets at columns x-1, x, x+1 (wrapped), row 0, plane 0
+    Pm = dst + xm;
+    P0 = dst + x;
+    Pp = dst + xp;
+    plane = (int)g.plane;
+    Wa = pmk(ph.Wpsi[0][0], ph.Wpsi[1][0]);
+    Wb = pmk(ph.Wpsi[0][1], ph.Wpsi[1][1]);
+    Wc = pmk(ph.Wpsi[0][2], ph.Wpsi[1][2]);
+    Wd = pmk(ph.Wpsi[0][3], ph.Wpsi[1][3]);
+    We = pmk(ph.Wpsi[0][4], ph.Wpsi[1][4]);
+    W2c = pmk(ph.W2psi[0][0], ph.W2psi[1][0]);
+    W2d = pmk(ph.W2psi[0][1], ph.W2psi[1][1]);
+    W2e = pmk(ph.W2psi[0][2], ph.W2psi[1][2]);
+    rho_ref = pmk(ph.rho_ref[0], ph.rho_ref[1]);
+    mrho0E = pmk(-ph.rho0 * ph.E[0], -ph.rho0 * ph.E[1]);
+    om = pmk(ph.omega[0], ph.omega[1]);
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+      Sx[k] = Sy[k] = Cx[k] = Cy[k] = lag_drho[k] = lag_psi[k] = pbc(C(0));
+    q = 0;
+    slot = ring % NSLOT;
+    parity = (ring / NSLOT) & 1;  // slot of row q and its phase parity
+    issued = 0;
+    bad = 0;
+  }
+
+  // the copy warp stages rows; a row's slot is refilled once every thread has
   // passed the barrier of the row three later (its collision is then done)
-  const bool producer = (warp == NCW);
-  int issued = 0;  // rows staged so far (same in every lane of the producer warp)
-  if (producer) {
+  __device__ __forceinline__ void prologue() {
+    if (!producer) return;
     for (; issued < NSLOT - 3 && issued < nstage; ++issued) {
       const int rp = ring + issued;
       issue_row<STORAGE>(src, stage + (rp % NSLOT) * SLOT, &bars[rp % NSLOT], g, x0,
@@ -184,49 +242,12 @@ __device__ __forceinline__ bool rows_range(
     }
   }
 
-  const bool compute = warp < NCW;
-  const int t = compute ? tid : 0;
-  const int x = x0 + t;
-  const bool active = compute && (x < g.nx);
-  int ecol;  // rho/psi column in the ext row [0, RX+4): column x0 - 2 + ecol
-  if (compute)
-    ecol = t + 2;
-  else
-    ecol = (lane < 2) ? lane : (lane < 4 ? RX + lane : -1);
-  const int xm = (x == 0) ? g.nx - 1 : x - 1;
-  const int xp = (x >= g.nx - 1) ? 0 : x + 1;
-  // push targets at columns x-1, x, x+1 (wrapped), row 0, plane 0
-  T2* const Pm = dst + xm;
-  T2* const P0 = dst + x;
-  T2* const Pp = dst + xp;
-
-  // per-species constants as pairs
-  const P Wa = pmk(ph.Wpsi[0][0], ph.Wpsi[1][0]), Wb = pmk(ph.Wpsi[0][1], ph.Wpsi[1][1]);
-  const P Wc = pmk(ph.Wpsi[0][2], ph.Wpsi[1][2]), Wd = pmk(ph.Wpsi[0][3], ph.Wpsi[1][3]);
-  const P We = pmk(ph.Wpsi[0][4], ph.Wpsi[1][4]);
-  const P W2c = pmk(ph.W2psi[0][0], ph.W2psi[1][0]), W2d = pmk(ph.W2psi[0][1], ph.W2psi[1][1]);
-  const P W2e = pmk(ph.W2psi[0][2], ph.W2psi[1][2]);
-  const P rho_ref = pmk(ph.rho_ref[0], ph.rho_ref[1]);
-  const P mrho0E = pmk(-ph.rho0 * ph.E[0], -ph.rho0 * ph.E[1]);
-  const P om = pmk(ph.omega[0], ph.omega[1]);
-
-  // accumulators (pairs): index k <-> row r - 2 + k of the row r just staged
-  P Sx[5], Sy[5], Cx[4], Cy[4];
-#pragma unroll
-  for (int k = 0; k < 5; ++k) Sx[k] = Sy[k] = pbc(C(0));
-#pragma unroll
-  for (int k = 0; k < 4; ++k) Cx[k] = Cy[k] = pbc(C(0));
-  // density deviations drho_s = sum_i d_i (kept as summed: rho_ref + drho
-  // rounds away the low bits that the mass-exact rest population needs)
-  P lag_drho[3], lag_psi[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) lag_drho[k] = lag_psi[k] = pbc(C(0));
-
-  int q = 0;
-  int slot = ring % NSLOT, parity = (ring / NSLOT) & 1;  // slot of row q and its phase parity
-  bool ok = true;
-#pragma unroll 1
-  for (; q < nstage; ++q) {
+  // One staged row (iteration q, q % 5 == R).  Returns false when a bounded
+  // wait gave up somewhere in the CTA.
+  template <int R>
+  __device__ __forceinline__ bool iter() {
+    constexpr int k0 = R % 5, k1 = (R + 1) % 5, k2 = (R + 2) % 5, k3 = (R + 3) % 5,
+                  k4 = (R + 4) % 5;
     if (!mbar_wait_bounded(&bars[slot], (uint32_t)parity)) {
       atomicExch(&status->timeout, 1u);
       *s_abort = 1;
@@ -248,10 +269,7 @@ __device__ __forceinline__ bool rows_range(
       rbuf[EXT + ecol] = my_psi;
     }
     __syncthreads();
-    if (*s_abort) {
-      ok = false;
-      break;
-    }
+    if (*s_abort) return false;
     // every thread has finished row q-1, so the slot of row q-3 is free
     if (producer && issued < nstage) {
       const int rp = ring + issued;
@@ -272,168 +290,159 @@ __device__ __forceinline__ bool rows_range(
         const P T2v = pfma(Wd, D1, pmul(W2e, D2));
         const P H1 = pfma(Wa, my_psi, pfma(Wb, P1, pmul(Wd, P2)));
         const P H2 = pfma(Wc, my_psi, pfma(Wd, P1, pmul(We, P2)));
-        Sx[0] = padd(Sx[0], T2v);
-        Sx[1] = padd(Sx[1], T1);
-        Sx[2] = padd(Sx[2], T0);
-        Sx[3] = padd(Sx[3], T1);
-        Sx[4] = T2v;
-        Sy[0] = pfma(pbc(C(2)), H2, Sy[0]);
-        Sy[1] = padd(Sy[1], H1);
-        Sy[3] = psub(Sy[3], H1);
-        Sy[4] = pmul(pbc(C(-2)), H2);
+        Sx[k0] = padd(Sx[k0], T2v);
+        Sx[k1] = padd(Sx[k1], T1);
+        Sx[k2] = padd(Sx[k2], T0);
+        Sx[k3] = padd(Sx[k3], T1);
+        Sx[k4] = T2v;
+        Sy[k0] = pfma(pbc(C(2)), H2, Sy[k0]);
+        Sy[k1] = padd(Sy[k1], H1);
+        Sy[k3] = psub(Sy[k3], H1);
+        Sy[k4] = pmul(pbc(C(-2)), H2);
         // inter-species term: the other species' density (the swapped pair) on belt 1
         const P* ro = rbuf;
         const P rm1 = ro[e - 1], rp1 = ro[e + 1];
         const P E1 = pswap(psub(rp1, rm1)), Q1 = pswap(padd(rp1, rm1));
         const P X0 = pmul(pbc(ph.gw[0]), E1), X1 = pmul(pbc(ph.gw[1]), E1);
         const P K = pfma(pbc(ph.gw[0]), pswap(my_rho), pmul(pbc(ph.gw[1]), Q1));
-        Cx[1] = padd(Cx[1], X1);
-        Cx[2] = padd(Cx[2], X0);
-        Cx[3] = X1;
-        Cy[1] = padd(Cy[1], K);
-        Cy[3] = psub(pbc(C(0)), K);
-        lag_drho[2] = my_drho;
-        lag_psi[2] = my_psi;
+        Cx[k1] = padd(Cx[k1], X1);
+        Cx[k2] = padd(Cx[k2], X0);
+        Cx[k3] = X1;
+        Cy[k1] = padd(Cy[k1], K);
+        Cy[k3] = psub(pbc(C(0)), K);
+        lag_drho[k2] = my_drho;
+        lag_psi[k2] = my_psi;
       }
-
       // ---- row o = r - 2 is complete: collide and push ----
-      if (q >= 4 && active) {
-        const int o = ylo + q - 4;
-        const int oslot = slot >= 2 ? slot - 2 : slot + NSLOT - 2;
-        const T2* orow = stage + oslot * SLOT + t + SOFF;
-        P d[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) d[i] = PS::ld(orow[i * SW]);
-        const P drho = lag_drho[0];
-        const P rho = padd(rho_ref, drho);
-        // G = -F: F_s = -psi_s S_s - rho_s C_s
-        const P Gx = pfma(lag_psi[0], Sx[0], pmul(rho, Cx[0]));
-        const P Gy = pfma(lag_psi[0], Sy[0], pmul(rho, Cy[0]));
-        const P jx = padd(padd(psub(d[1], d[3]), psub(d[5], d[6])), psub(d[8], d[7]));
-        const P jy = padd(padd(psub(d[2], d[4]), psub(d[5], d[8])), psub(d[6], d[7]));
-        // common velocity u = sum_s j_s/tau_s / sum_s rho_s/tau_s
-        const P rw = pmul(rho, om), jxw = pmul(jx, om), jyw = pmul(jy, om);
-        const C inv = div_c<C>(C(1), rw.x + rw.y);
-        const C ux = (jxw.x + jxw.y) * inv, uy = (jyw.x + jyw.y) * inv;
-        // shifted velocity v_s = u + tau_s F_s / rho_s = u - (tau_s/rho_s) G_s
-        P k = pbc(C(0));
-        if (rho.x > C(0)) k.x = -div_c<C>(ph.tau[0], rho.x); else ++bad;
-        if (rho.y > C(0)) k.y = -div_c<C>(ph.tau[1], rho.y); else ++bad;
-        const P vx = pfma(k, Gx, pbc(ux));
-        const P vy = pfma(k, Gy, pbc(uy));
-        // BGK relaxation toward the shifted equilibrium (factored form, see lb_site.cuh)
-        {
-          const P keep = psub(pbc(C(1)), om);
-          const P v2 = pfma(vx, vx, pmul(vy, vy));
-          const P tt = pfma(pmul(pbc(C(-1.5)), rho), v2, drho);
-          const P B0 = pmul(pmul(om, pbc(wq<C>(0))), tt);
-          const P B1 = pmul(pmul(om, pbc(wq<C>(1))), tt);
-          const P B2 = pmul(pmul(om, pbc(wq<C>(5))), tt);
-          const P a1 = pmul(pmul(om, pbc(C(3) * wq<C>(1))), rho);
-          const P b1 = pmul(pmul(om, pbc(C(4.5) * wq<C>(1))), rho);
-          const P a2 = pmul(pmul(om, pbc(C(3) * wq<C>(5))), rho);
-          const P b2 = pmul(pmul(om, pbc(C(4.5) * wq<C>(5))), rho);
-          d[0] = pfma(keep, d[0], B0);
-          const P ex = pfma(pmul(b1, vx), vx, B1), ax = pmul(a1, vx);
-          const P ey = pfma(pmul(b1, vy), vy, B1), ay = pmul(a1, vy);
-          d[1] = pfma(keep, d[1], padd(ex, ax));
-          d[3] = pfma(keep, d[3], psub(ex, ax));
-          d[2] = pfma(keep, d[2], padd(ey, ay));
-          d[4] = pfma(keep, d[4], psub(ey, ay));
-          const P s1 = padd(vx, vy), s2 = psub(vx, vy);
-          const P e1 = pfma(pmul(b2, s1), s1, B2), ad1 = pmul(a2, s1);
-          const P e2 = pfma(pmul(b2, s2), s2, B2), ad2 = pmul(a2, s2);
-          d[5] = pfma(keep, d[5], padd(e1, ad1));
-          d[7] = pfma(keep, d[7], psub(e1, ad1));
-          d[8] = pfma(keep, d[8], padd(e2, ad2));
-          d[6] = pfma(keep, d[6], psub(e2, ad2));
-        }
-        if (STORAGE != LB_F64) {
-          // mass-exact rest population: the collision conserves rho_s exactly,
-          // so give the rest population what the eight moving ones (as stored)
-          // leave of drho; one rounding per site instead of a biased sum of nine
-          P r8 = PS::ld(PS::st(d[1]));
-#pragma unroll
-          for (int i = 2; i < 9; ++i) r8 = padd(r8, PS::ld(PS::st(d[i])));
-          d[0] = psub(drho, r8);
-        }
-        // 16-bit storages round the rest population stochastically; the bits are
-        // hashed from the site and its relaxed populations (deterministic runs)
-        uint32_t rbits = 0;
-        if (sizeof(T2) == 4)
-          rbits = mix32(__float_as_uint((float)d[1].x) ^ (__float_as_uint((float)d[6].y) << 7) ^
-                        ((uint32_t)x * 0x9E3779B1u) ^ ((uint32_t)o * 0x85EBCA77u));
-        const bool wall = (g.boundary == LB_COUETTE) && (o == 0 || o == g.ny - 1);
-        if (!wall) {
-          // row and plane offsets are the same for every thread of the CTA
-          const int om_ = (o == 0) ? g.ny - 1 : o - 1;
-          const int op_ = (o == g.ny - 1) ? 0 : o + 1;
-          const long long Om = (long long)om_ * g.pitch, O0 = (long long)o * g.pitch,
-                          Op = (long long)op_ * g.pitch;
-          // streaming (evict-first) stores: the new state is read back only next step
-          __stcs(&P0[O0], PS::st_sr(d[0], rbits));
-          __stcs(&Pp[1 * g.plane + O0], PS::st(d[1]));
-          __stcs(&P0[2 * g.plane + Op], PS::st(d[2]));
-          __stcs(&Pm[3 * g.plane + O0], PS::st(d[3]));
-          __stcs(&P0[4 * g.plane + Om], PS::st(d[4]));
-          __stcs(&Pp[5 * g.plane + Op], PS::st(d[5]));
-          __stcs(&Pm[6 * g.plane + Op], PS::st(d[6]));
-          __stcs(&Pm[7 * g.plane + Om], PS::st(d[7]));
-          __stcs(&Pp[8 * g.plane + Om], PS::st(d[8]));
-        } else {
-          // Ladd: a link through the wall comes back along opp(i) at the same
-          // site, less 2 w_i rho_s (c_i . U_w)/cs2 per species
-#pragma unroll
-          for (int i = 1; i < 9; ++i) {
-            const int yd = o + Q9::cy(i);
-            if (yd < 0 || yd >= g.ny) {
-              const C Uw = (yd >= g.ny) ? ph.Uwall : -ph.Uwall;
-              d[i] = pfma(pbc(-C(6) * wq<C>(i) * C(Q9::cx(i)) * Uw), rho, d[i]);
-            }
-          }
-          if (STORAGE != LB_F64) {  // mass-exact again, with the values the wall sends back
-            P r8 = PS::ld(PS::st(d[1]));
-#pragma unroll
-            for (int i = 2; i < 9; ++i) r8 = padd(r8, PS::ld(PS::st(d[i])));
-            d[0] = psub(drho, r8);
-          }
-#pragma unroll
-          for (int i = 0; i < 9; ++i) {
-            const int yd = o + Q9::cy(i);
-            if (yd < 0 || yd >= g.ny) {
-              P0[(long long)Q9::opp(i) * g.plane + (long long)o * g.pitch] = PS::st(d[i]);
-            } else {
-              T2* Pc = Q9::cx(i) == 0 ? P0 : (Q9::cx(i) > 0 ? Pp : Pm);
-              Pc[(long long)i * g.plane + (long long)yd * g.pitch] =
-                  i == 0 ? PS::st_sr(d[i], rbits) : PS::st(d[i]);
-            }
-          }
-        }
-      }
-      // ---- slide the windows by one row ----
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        Sx[k] = Sx[k + 1];
-        Sy[k] = Sy[k + 1];
-      }
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        Cx[k] = Cx[k + 1];
-        Cy[k] = Cy[k + 1];
-      }
-      lag_drho[0] = lag_drho[1];
-      lag_drho[1] = lag_drho[2];
-      lag_psi[0] = lag_psi[1];
-      lag_psi[1] = lag_psi[2];
+      if (q >= 4 && active) collide(ylo + q - 4, Sx[k0], Sy[k0], Cx[k0], Cy[k0], lag_drho[k0],
+                                    lag_psi[k0]);
     }
     if (++slot == NSLOT) {
       slot = 0;
       parity ^= 1;
     }
+    ++q;
+    return true;
   }
-  if (!ok && producer && lane == 0) {
-    // drain: wait (bounded) for the rows staged but not consumed, so that no
-    // copy is still writing into this CTA's shared memory when it exits
+
+  __device__ __forceinline__ void collide(int o, P Sx0, P Sy0, P Cx0, P Cy0, P drho, P psi0) {
+    const int oslot = slot >= 2 ? slot - 2 : slot + NSLOT - 2;
+    const T2* orow = stage + oslot * SLOT + t + SOFF;
+    P d[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d[i] = PS::ld(orow[i * SW]);
+    const P rho = padd(rho_ref, drho);
+    // G = -F: F_s = -psi_s S_s - rho_s C_s
+    const P Gx = pfma(psi0, Sx0, pmul(rho, Cx0));
+    const P Gy = pfma(psi0, Sy0, pmul(rho, Cy0));
+    const P jx = padd(padd(psub(d[1], d[3]), psub(d[5], d[6])), psub(d[8], d[7]));
+    const P jy = padd(padd(psub(d[2], d[4]), psub(d[5], d[8])), psub(d[6], d[7]));
+    // common velocity u = sum_s j_s/tau_s / sum_s rho_s/tau_s
+    const P rw = pmul(rho, om), jxw = pmul(jx, om), jyw = pmul(jy, om);
+    const C inv = div_c<C>(C(1), rw.x + rw.y);
+    const C ux = (jxw.x + jxw.y) * inv, uy = (jyw.x + jyw.y) * inv;
+    // shifted velocity v_s = u + tau_s F_s / rho_s = u - (tau_s/rho_s) G_s
+    // (branch-free: the quotient of a non-positive density is discarded)
+    const bool posA = rho.x > C(0), posB = rho.y > C(0);
+    bad += (posA ? 0 : 1) + (posB ? 0 : 1);
+    P k;
+    k.x = posA ? -div_c<C>(ph.tau[0], rho.x) : C(0);
+    k.y = posB ? -div_c<C>(ph.tau[1], rho.y) : C(0);
+    const P vx = pfma(k, Gx, pbc(ux));
+    const P vy = pfma(k, Gy, pbc(uy));
+    // BGK relaxation toward the shifted equilibrium (factored form, see lb_site.cuh)
+    {
+      const P keep = psub(pbc(C(1)), om);
+      const P v2 = pfma(vx, vx, pmul(vy, vy));
+      const P tt = pfma(pmul(pbc(C(-1.5)), rho), v2, drho);
+      const P B0 = pmul(pmul(om, pbc(wq<C>(0))), tt);
+      const P B1 = pmul(pmul(om, pbc(wq<C>(1))), tt);
+      const P B2 = pmul(pmul(om, pbc(wq<C>(5))), tt);
+      const P a1 = pmul(pmul(om, pbc(C(3) * wq<C>(1))), rho);
+      const P b1 = pmul(pmul(om, pbc(C(4.5) * wq<C>(1))), rho);
+      const P a2 = pmul(pmul(om, pbc(C(3) * wq<C>(5))), rho);
+      const P b2 = pmul(pmul(om, pbc(C(4.5) * wq<C>(5))), rho);
+      d[0] = pfma(keep, d[0], B0);
+      const P ex = pfma(pmul(b1, vx), vx, B1), ax = pmul(a1, vx);
+      const P ey = pfma(pmul(b1, vy), vy, B1), ay = pmul(a1, vy);
+      d[1] = pfma(keep, d[1], padd(ex, ax));
+      d[3] = pfma(keep, d[3], psub(ex, ax));
+      d[2] = pfma(keep, d[2], padd(ey, ay));
+      d[4] = pfma(keep, d[4], psub(ey, ay));
+      const P s1 = padd(vx, vy), s2 = psub(vx, vy);
+      const P e1 = pfma(pmul(b2, s1), s1, B2), ad1 = pmul(a2, s1);
+      const P e2 = pfma(pmul(b2, s2), s2, B2), ad2 = pmul(a2, s2);
+      d[5] = pfma(keep, d[5], padd(e1, ad1));
+      d[7] = pfma(keep, d[7], psub(e1, ad1));
+      d[8] = pfma(keep, d[8], padd(e2, ad2));
+      d[6] = pfma(keep, d[6], psub(e2, ad2));
+    }
+    if (STORAGE != LB_F64) {
+      // mass-exact rest population: the collision conserves rho_s exactly,
+      // so give the rest population what the eight moving ones (as stored)
+      // leave of drho; one rounding per site instead of a biased sum of nine
+      P r8 = PS::ld(PS::st(d[1]));
+#pragma unroll
+      for (int i = 2; i < 9; ++i) r8 = padd(r8, PS::ld(PS::st(d[i])));
+      d[0] = psub(drho, r8);
+    }
+    // 16-bit storages round the rest population stochastically; the bits are
+    // hashed from the site and its relaxed populations (deterministic runs)
+    uint32_t rbits = 0;
+    if (sizeof(T2) == 4)
+      rbits = mix32(__float_as_uint((float)d[1].x) ^ (__float_as_uint((float)d[6].y) << 7) ^
+                    ((uint32_t)x * 0x9E3779B1u) ^ ((uint32_t)o * 0x85EBCA77u));
+    const bool wall = (g.boundary == LB_COUETTE) && (o == 0 || o == g.ny - 1);
+    if (!wall) {
+      // row and plane offsets (32-bit: rows_geometry_ok bounds 9 planes
+      // below 2^31 sites) are the same for every thread of the CTA
+      const int om_ = (o == 0) ? g.ny - 1 : o - 1;
+      const int op_ = (o == g.ny - 1) ? 0 : o + 1;
+      const int Om = om_ * g.pitch, O0 = o * g.pitch, Op = op_ * g.pitch;
+      // streaming (evict-first) stores: the new state is read back only next step
+      __stcs(&P0[O0], PS::st_sr(d[0], rbits));
+      __stcs(&Pp[1 * plane + O0], PS::st(d[1]));
+      __stcs(&P0[2 * plane + Op], PS::st(d[2]));
+      __stcs(&Pm[3 * plane + O0], PS::st(d[3]));
+      __stcs(&P0[4 * plane + Om], PS::st(d[4]));
+      __stcs(&Pp[5 * plane + Op], PS::st(d[5]));
+      __stcs(&Pm[6 * plane + Op], PS::st(d[6]));
+      __stcs(&Pm[7 * plane + Om], PS::st(d[7]));
+      __stcs(&Pp[8 * plane + Om], PS::st(d[8]));
+    } else {
+      // Ladd: a link through the wall comes back along opp(i) at the same
+      // site, less 2 w_i rho_s (c_i . U_w)/cs2 per species
+#pragma unroll
+      for (int i = 1; i < 9; ++i) {
+        const int yd = o + Q9::cy(i);
+        if (yd < 0 || yd >= g.ny) {
+          const C Uw = (yd >= g.ny) ? ph.Uwall : -ph.Uwall;
+          d[i] = pfma(pbc(-C(6) * wq<C>(i) * C(Q9::cx(i)) * Uw), rho, d[i]);
+        }
+      }
+      if (STORAGE != LB_F64) {  // mass-exact again, with the values the wall sends back
+        P r8 = PS::ld(PS::st(d[1]));
+#pragma unroll
+        for (int i = 2; i < 9; ++i) r8 = padd(r8, PS::ld(PS::st(d[i])));
+        d[0] = psub(drho, r8);
+      }
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const int yd = o + Q9::cy(i);
+        if (yd < 0 || yd >= g.ny) {
+          P0[Q9::opp(i) * plane + o * g.pitch] = PS::st(d[i]);
+        } else {
+          T2* Pc = Q9::cx(i) == 0 ? P0 : (Q9::cx(i) > 0 ? Pp : Pm);
+          Pc[i * plane + yd * g.pitch] = i == 0 ? PS::st_sr(d[i], rbits) : PS::st(d[i]);
+        }
+      }
+    }
+  }
+
+  // drain: wait (bounded) for the rows staged but not consumed, so that no
+  // copy is still writing into this CTA's shared memory when it exits
+  __device__ __forceinline__ void drain() {
+    if (!(producer && lane == 0)) return;
     for (int k = q; k < issued; ++k) {
       const int rp = ring + k;
       const long long t0 = clock64();
@@ -442,7 +451,34 @@ __device__ __forceinline__ bool rows_range(
       }
     }
   }
-  ring += nstage;
+};
+
+// One CTA, one work range: columns x0 .. x0+RX-1 (clipped to nx), output rows
+// ylo .. yhi-1 of the lattice (src -> dst).  `ring` is the position of the
+// next staged row in the CTA's slot ring (identical in every thread); on
+// entry every slot is free.  Returns false if a bounded wait gave up (after
+// draining the copies this range issued).
+template <int STORAGE>
+__device__ __forceinline__ bool rows_range(
+    const typename PairStore<STORAGE>::T2* __restrict__ src,
+    typename PairStore<STORAGE>::T2* __restrict__ dst, const Geom& g,
+    const Phys<typename Store<STORAGE>::C>& ph, int x0, int ylo, int yhi,
+    typename PairStore<STORAGE>::T2* stage, typename PairOf<typename Store<STORAGE>::C>::P* rowbuf0,
+    uint64_t* bars, int& ring, int* s_abort, Status* status, int& bad) {
+  RowsLoop<STORAGE> L(src, dst, g, ph, x0, ylo, yhi, stage, rowbuf0, bars, ring, s_abort, status);
+  L.prologue();
+  bool ok = true;
+#pragma unroll 1
+  while (L.q < L.nstage) {
+    if (!(ok = L.template iter<0>()) || L.q >= L.nstage) break;
+    if (!(ok = L.template iter<1>()) || L.q >= L.nstage) break;
+    if (!(ok = L.template iter<2>()) || L.q >= L.nstage) break;
+    if (!(ok = L.template iter<3>()) || L.q >= L.nstage) break;
+    if (!(ok = L.template iter<4>())) break;
+  }
+  if (!ok) L.drain();
+  bad += L.bad;
+  ring += L.nstage;
   return ok;
 }
 
@@ -590,7 +626,9 @@ bool rows_geometry_ok(const Geom& g, int storage) {
   if (pair_bytes == 0) return false;
   const int a = pair_bytes >= 16 ? 1 : 16 / pair_bytes;  // sites per 16 bytes
   // 16-byte aligned rows and seams; the periodic window may wrap several times
-  return (g.nx % a == 0) && (g.pitch % a == 0) && (g.nx >= 8) && (g.ny >= 5);
+  // element offsets within a buffer are 32-bit: 9 planes below 2^31 sites
+  return (g.nx % a == 0) && (g.pitch % a == 0) && (g.nx >= 8) && (g.ny >= 5) &&
+         9 * g.plane < (1LL << 31);
 }
 
 bool rows_supported(const Geom& g, int storage) {
