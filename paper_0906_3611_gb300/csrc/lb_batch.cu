@@ -119,18 +119,18 @@ static void drop_graph(lb_batch* b) {
 static int rebuild_items(lb_batch* b) {
   std::vector<WorkItem> items;
   std::vector<int> counts(b->capacity, 0);
-  const int rx = rows_strip_width();
   for (int k = 0; k < b->capacity; ++k) {
     const Slot& s = b->slots[k];
     if (!s.used) continue;
-    const int nstrips = (s.nx + rx - 1) / rx;
+    const int nstrips = rows_nstrips(s.nx);
     int nranges = (s.ny + b->rows_per_item / 2) / b->rows_per_item;
     if (nranges < 1) nranges = 1;
     for (int r = 0; r < nranges; ++r) {
       const int ylo = (int)((long long)r * s.ny / nranges);
       const int yhi = (int)((long long)(r + 1) * s.ny / nranges);
       for (int j = 0; j < nstrips; ++j) {
-        items.push_back(WorkItem{k, j * rx, ylo, yhi});
+        items.push_back(WorkItem{k, rows_strip_x0(j, nstrips, s.nx),
+                                 rows_strip_x0(j + 1, nstrips, s.nx), ylo, yhi});
         ++counts[k];
       }
     }

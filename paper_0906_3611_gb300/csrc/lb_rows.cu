@@ -1,64 +1,74 @@
 // lb_rows.cu -- row-streaming fused step kernel (the bandwidth path).
 //
-// Each CTA owns a strip of RX = 128 columns and a contiguous range of rows,
-// and walks down the rows once.  Row r of the state f(t) (the 9 direction
-// planes, both species of each site side by side, columns x0-SOFF ..
-// x0+RX+SOFF-1, periodic in x) is staged in shared memory by bulk
+// Each CTA owns a strip of RX = 128 columns [x0, x1) and a contiguous range
+// of rows, and walks down the rows once.  Row r of the state f(t) (the 9
+// direction planes, both species of each site side by side, columns
+// x0-SOFF .. x0+RX+SOFF-1, periodic in x) is staged in shared memory by bulk
 // asynchronous copies (the TMA engine, cp.async.bulk) into a ring of NSLOT
-// slots guarded by mbarriers, NSLOT-4 rows ahead of use.
+// slots.  A "full" mbarrier per slot counts the copied bytes; an "empty"
+// mbarrier per slot counts the compute warps that are done with it.
 //
-// One thread serves one column and carries both species as a pair (packed
-// two-wide FP32 arithmetic).  For every staged row it forms rho and
-// psi = rho0 (1 - exp(-rho/rho0)) (Eq. (PSI)) of its column; the row is
-// shared through shared memory (double-buffered, one barrier per row), and
-// the thread adds the row's contribution to the 5 x 5 force stencil of its
-// column (Eq. (FORCE), Table I) into register accumulators of the five rows
-// the row touches.  The stencil is separable per row: with
-// D1 = psi(x+1)-psi(x-1), D2 = psi(x+2)-psi(x-2), P1 = psi(x+1)+psi(x-1),
-// P2 = psi(x+2)+psi(x-2),
+// Warp specialisation: warps 0..NCW-1 compute, warp NCW only stages rows
+// (it refills a slot as soon as every compute warp has released it).  The
+// compute warps never wait for one another: each one serves 32 columns, forms
+// rho and psi = rho0 (1 - exp(-rho/rho0)) (Eq. (PSI)) of its columns plus two
+// halo columns on each side (recomputed by four of its lanes) into a shared
+// row buffer of its own, and carries both species of a site as a pair
+// (packed two-wide FP32 arithmetic).  Each staged row adds its contribution
+// to the 5 x 5 force stencil (Eq. (FORCE), Table I) of its column into
+// register accumulators of the five rows it touches.  The stencil is
+// separable per row: with D1 = psi(x+1)-psi(x-1), D2 = psi(x+2)-psi(x-2),
+// P1 = psi(x+1)+psi(x-1), P2 = psi(x+2)+psi(x-2),
 //   sum_c W(c) psi(r+c) c_x = sum_dy [W(1,dy) D1 + 2 W(2,dy) D2](y+dy)
 //   sum_c W(c) psi(r+c) c_y = [H1(y+1) - H1(y-1)] + 2 [H2(y+2) - H2(y-2)],
 //   H1 = W(0,1) psi + W(1,1) P1 + W(2,1) P2,  H2 = W(0,2) psi + W(1,2) P1 + W(2,2) P2,
 // and likewise on belt 1 for the inter-species density term (the other
-// species' density: the pair swapped).  When the row two below has all its
-// contributions, its sites collide (the shifted BGK of Eq. (be)) with their
-// populations re-read from the staged slot, and push f*_i to r + c_i in
-// global memory (Ladd bounce-back at Couette walls).  Every population is
-// read from DRAM once and written once; the halos (2 columns, 2+2 rows per
-// range) are served by L2 or recomputed.
+// species' density: the pair swapped).  When the row two above the staged one
+// has all its contributions, its sites collide (the shifted BGK of Eq. (be))
+// with their populations re-read from the staged slot, and push f*_i to
+// r + c_i in global memory (Ladd bounce-back at Couette walls).  Every
+// population is read from DRAM once and written once; the halos (SOFF
+// columns, 2+2 rows per range) are served by L2.
 //
-// Warps 0..NCW-1 compute; warp NCW issues the bulk copies and forms rho/psi of
-// the four halo columns.  Every mbarrier wait is bounded: on timeout the kernel
-// sets the status word, drains its own copies (bounded) and leaves.
+// Every mbarrier wait is bounded: on timeout the kernel sets the status word,
+// raises the CTA's abort flag, drains its own copies (bounded) and leaves.
 #include "lb_pair.cuh"
 #include "lb_rows.h"
 #include "lb_site.cuh"
 
 namespace lbk {
 
-constexpr int RX = 128;            // interior columns per strip (a multiple of 32)
+constexpr int RX = 128;            // strip columns (a multiple of 32)
 constexpr int NCW = RX / 32;       // compute warps
-constexpr int RTHREADS = RX + 32;  // compute warps + 1 copy/halo warp
+constexpr int RTHREADS = RX + 32;  // compute warps + 1 staging warp
+constexpr int WEXT = 32 + 4;       // a compute warp's row buffer: 32 columns + 2 + 2 halo
 
 // SOFF: halo sites staged on each side (>= 2, a 16-byte multiple of pairs);
-// NSLOT: ring depth; MINB: CTAs per SM the register budget is sized for.
+// NSLOT: ring depth; MINB: CTAs per SM the register budget is sized for;
+// PIPE: form the next row's rho/psi together with the current collision
+// (hides latency; costs live registers, which the 16-bit storages' longer
+// load/convert code cannot spare).
 template <int STORAGE>
 struct RowsCfg;
 template <>
 struct RowsCfg<LB_F64> {
   static constexpr int SOFF = 2, NSLOT = 5, MINB = 2;  // 16-byte pairs
+  static constexpr bool PIPE = true;
 };
 template <>
 struct RowsCfg<LB_F32> {
   static constexpr int SOFF = 2, NSLOT = 7, MINB = 3;  // 8-byte pairs
+  static constexpr bool PIPE = true;
 };
 template <>
 struct RowsCfg<LB_BF16_DEV> {
   static constexpr int SOFF = 4, NSLOT = 9, MINB = 3;  // 4-byte pairs
+  static constexpr bool PIPE = false;
 };
 template <>
 struct RowsCfg<LB_F16_DEV> {
   static constexpr int SOFF = 4, NSLOT = 9, MINB = 3;
+  static constexpr bool PIPE = false;
 };
 
 template <int STORAGE>
@@ -71,7 +81,7 @@ constexpr size_t rows_smem_bytes() {
   using T2 = typename PairStore<STORAGE>::T2;
   using P = typename PairOf<typename Store<STORAGE>::C>::P;
   return (size_t)RowsCfg<STORAGE>::NSLOT * 9 * stage_width<STORAGE>() * sizeof(T2) +
-         2 * 2 * (RX + 4) * sizeof(P) + 8 * RowsCfg<STORAGE>::NSLOT;
+         (size_t)NCW * 2 * WEXT * sizeof(P) + 2 * 8 * RowsCfg<STORAGE>::NSLOT;
 }
 
 // ---- mbarrier / bulk-copy primitives (PTX) ----
@@ -88,6 +98,9 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                "r"(bytes)
                : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t done;
@@ -106,6 +119,19 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (clock64() - t0 > (1LL << 31)) return false;
+  }
+  return true;
+}
+// Bounded wait with exponential sleep between polls, for a waiter that is far
+// ahead of the event (the staging warp): it then takes few issue slots.
+__device__ __forceinline__ bool mbar_wait_backoff(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  unsigned ns = 32;
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > (1LL << 31)) return false;
+    __nanosleep(ns);
+    if (ns < 512) ns *= 2;
   }
   return true;
 }
@@ -137,7 +163,7 @@ __device__ __forceinline__ void issue_row(const typename PairStore<STORAGE>::T2*
   const T2* pl = src + (long long)lane * g.plane + (long long)ys * g.pitch;
   T2* d = slot + lane * SW;
   int gx = x0 - SOFF;
-  if (gx < 0) gx += g.nx;
+  while (gx < 0) gx += g.nx;
   for (int c = 0; c < SW;) {
     const int len = min(SW - c, g.nx - gx);
     bulk_g2s(d + c, pl + gx, (uint32_t)(len * sizeof(T2)), bar);
@@ -146,11 +172,40 @@ __device__ __forceinline__ void issue_row(const typename PairStore<STORAGE>::T2*
   }
 }
 
-// The per-thread state of one work range.  The stencil accumulators and the
-// lagged rho/psi rows are windows over rows r-2 .. r+2 of the row r staged in
-// the current iteration; logical index k of a window lives in register slot
-// (k + R) % 5, R = (iteration) % 5, and the row loop is unrolled five times,
-// so that the windows slide by renaming registers instead of moving them.
+// Shared-memory layout of a CTA.
+template <int STORAGE>
+struct RowsSmem {
+  using T2 = typename PairStore<STORAGE>::T2;
+  using P = typename PairOf<typename Store<STORAGE>::C>::P;
+  static constexpr int NSLOT = RowsCfg<STORAGE>::NSLOT;
+  static constexpr int SLOT = 9 * stage_width<STORAGE>();
+  T2* stage;      // NSLOT slots of SLOT pairs
+  P* rowbuf;      // per compute warp: WEXT rho pairs, WEXT psi pairs
+  uint64_t* full;   // NSLOT mbarriers: bytes of the staged row landed
+  uint64_t* empty;  // NSLOT mbarriers: every compute warp released the slot
+  __device__ __forceinline__ explicit RowsSmem(unsigned char* smem) {
+    stage = reinterpret_cast<T2*>(smem);
+    size_t off = (size_t)NSLOT * SLOT * sizeof(T2);
+    rowbuf = reinterpret_cast<P*>(smem + off);
+    off += (size_t)NCW * 2 * WEXT * sizeof(P);
+    full = reinterpret_cast<uint64_t*>(smem + off);
+    empty = full + NSLOT;
+  }
+  __device__ __forceinline__ void init() {  // thread 0, before the first __syncthreads
+    for (int k = 0; k < NSLOT; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], NCW);
+    }
+    mbar_fence_init();
+  }
+};
+
+// One work range of one CTA.  The stencil accumulators and the lagged rho/psi
+// rows of a compute thread are windows over rows r-2 .. r+2 of the row r
+// staged in the current iteration; logical index k of a window lives in
+// register slot (k + R) % 5, R = (iteration) % 5, so that the windows slide
+// by renaming registers instead of moving them (the window update is
+// specialised per rotation; staging and collision are shared).
 template <int STORAGE>
 struct RowsLoop {
   using PS = PairStore<STORAGE>;
@@ -161,48 +216,37 @@ struct RowsLoop {
   static constexpr int NSLOT = RowsCfg<STORAGE>::NSLOT;
   static constexpr int SW = stage_width<STORAGE>();
   static constexpr int SLOT = 9 * SW;
-  static constexpr int EXT = RX + 4;
 
   const T2* __restrict__ src;
   const Geom& g;
   const Phys<C>& ph;
-  T2* stage;
-  P* rowbuf0;
-  uint64_t* bars;
+  const RowsSmem<STORAGE>& sm;
   int* s_abort;
   Status* status;
   int x0, ylo, nstage, ring;
-  // this thread
-  int lane, t, x, ecol, plane;
-  bool producer, compute, active;
+  // this thread (a compute thread serves column x = x0 + t)
+  int warp, lane, t, x, plane;
+  bool active;
   T2 *Pm, *P0, *Pp;
+  P* wbuf;  // this warp's row buffer: [0, WEXT) rho, [WEXT, 2 WEXT) psi
   // per-species constants as pairs
   P Wa, Wb, Wc, Wd, We, W2c, W2d, W2e, rho_ref, mrho0E, om;
   // windows (see above) and loop state
   P Sx[5], Sy[5], Cx[5], Cy[5], lag_drho[5], lag_psi[5];
-  int q, slot, parity, issued, bad;
+  int bad;
 
   __device__ __forceinline__ RowsLoop(const T2* __restrict__ src_, T2* __restrict__ dst,
-                                      const Geom& g_, const Phys<C>& ph_, int x0_, int ylo_,
-                                      int yhi, T2* stage_, P* rowbuf0_, uint64_t* bars_,
-                                      int ring_, int* s_abort_, Status* status_)
-      : src(src_), g(g_), ph(ph_), stage(stage_), rowbuf0(rowbuf0_), bars(bars_),
-        s_abort(s_abort_), status(status_), x0(x0_), ylo(ylo_), nstage((yhi - ylo_) + 4),
-        ring(ring_) {
-    const int tid = threadIdx.x;
-    const int warp = tid >> 5;
-    lane = tid & 31;
-    producer = (warp == NCW);
-    compute = warp < NCW;
-    t = compute ? tid : 0;
+                                      const Geom& g_, const Phys<C>& ph_, int x0_, int x1,
+                                      int ylo_, int yhi, const RowsSmem<STORAGE>& sm_, int ring_,
+                                      int* s_abort_, Status* status_)
+      : src(src_), g(g_), ph(ph_), sm(sm_), s_abort(s_abort_), status(status_), x0(x0_),
+        ylo(ylo_), nstage((yhi - ylo_) + 4), ring(ring_) {
+    warp = threadIdx.x >> 5;
+    lane = threadIdx.x & 31;
+    t = (warp < NCW) ? (int)threadIdx.x : 0;
     x = x0 + t;
-    active = compute && (x < g.nx);
-    // rho/psi column in the ext row [0, RX+4): column x0 - 2 + ecol; the copy
-    // warp's lanes 0..3 form the four halo columns
-    if (compute)
-      ecol = t + 2;
-    else
-      ecol = (lane < 2) ? lane : (lane < 4 ? RX + lane : -1);
+    active = (warp < NCW) && (x < x1);
+    if (!active) x = x0;  // (keeps the push targets below in range)
     const int xm = (x == 0) ? g.nx - 1 : x - 1;
     const int xp = (x >= g.nx - 1) ? 0 : x + 1;
     // push targets at columns x-1, x, x+1 (wrapped), row 0, plane 0
@@ -210,6 +254,7 @@ struct RowsLoop {
     P0 = dst + x;
     Pp = dst + xp;
     plane = (int)g.plane;
+    wbuf = sm.rowbuf + (warp < NCW ? warp : 0) * 2 * WEXT;
     Wa = pmk(ph.Wpsi[0][0], ph.Wpsi[1][0]);
     Wb = pmk(ph.Wpsi[0][1], ph.Wpsi[1][1]);
     Wc = pmk(ph.Wpsi[0][2], ph.Wpsi[1][2]);
@@ -224,114 +269,262 @@ struct RowsLoop {
 #pragma unroll
     for (int k = 0; k < 5; ++k)
       Sx[k] = Sy[k] = Cx[k] = Cy[k] = lag_drho[k] = lag_psi[k] = pbc(C(0));
-    q = 0;
-    slot = ring % NSLOT;
-    parity = (ring / NSLOT) & 1;  // slot of row q and its phase parity
-    issued = 0;
     bad = 0;
   }
 
-  // the copy warp stages rows; a row's slot is refilled once every thread has
-  // passed the barrier of the row three later (its collision is then done)
-  __device__ __forceinline__ void prologue() {
-    if (!producer) return;
-    for (; issued < NSLOT - 3 && issued < nstage; ++issued) {
-      const int rp = ring + issued;
-      issue_row<STORAGE>(src, stage + (rp % NSLOT) * SLOT, &bars[rp % NSLOT], g, x0,
-                         ylo - 2 + issued, lane);
+  __device__ __forceinline__ int slot_of(int j) const { return (ring + j) % NSLOT; }
+  __device__ __forceinline__ uint32_t round_of(int j) const { return (uint32_t)((ring + j) / NSLOT); }
+
+  // ---- the staging warp: stage rows 0 .. nstage-1, each into a slot that
+  // every compute warp has released ----
+  __device__ __forceinline__ void produce() {
+    int j = 0;
+    for (; j < nstage; ++j) {
+      const int s = slot_of(j);
+      const uint32_t rnd = round_of(j);
+      if (rnd > 0 && !mbar_wait_backoff(&sm.empty[s], (rnd - 1) & 1)) {
+        if (lane == 0) {
+          atomicExch(&status->timeout, 1u);
+          *s_abort = 1;
+        }
+        break;
+      }
+      if (*(volatile int*)s_abort) break;
+      issue_row<STORAGE>(src, sm.stage + s * SLOT, &sm.full[s], g, x0, ylo - 2 + j, lane);
+    }
+    // on abort, wait (bounded) for the copies in flight, so that none is still
+    // writing into this CTA's shared memory when it moves on or exits
+    if (j < nstage && lane == 0) {
+      for (int k = (j > NSLOT ? j - NSLOT : 0); k < j; ++k) {
+        const long long t0 = clock64();
+        while (!mbar_try_wait(&sm.full[slot_of(k)], round_of(k) & 1)) {
+          if (clock64() - t0 > (1LL << 31)) break;
+        }
+      }
     }
   }
 
-  // One staged row (iteration q, q % 5 == R).  Returns false when a bounded
-  // wait gave up somewhere in the CTA.
+  // rho, drho and psi pairs of staged column c (0 .. SW-1) of a staged row
+  __device__ __forceinline__ void column(const T2* srow, int c, P& rho, P& psi, P& drho) const {
+    const T2* p = srow + c;
+    P v[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) v[i] = PS::ld(p[i * SW]);
+    // pairwise sum (a shorter dependency chain than a running sum)
+    const P a = padd(padd(padd(v[0], v[1]), padd(v[2], v[3])),
+                     padd(padd(v[4], v[5]), padd(v[6], padd(v[7], v[8]))));
+    drho = a;
+    rho = padd(rho_ref, a);
+    const P ex = pmk(exp_c<C>(-a.x * ph.inv_rho0), exp_c<C>(-a.y * ph.inv_rho0));
+    psi = pfma(mrho0E, ex, pbc(ph.rho0));
+  }
+
+  // Row r's contribution to the force stencil of rows r-2 .. r+2, with the
+  // windows rotated by R = q % 5; hands back the completed row r-2 (logical 0).
   template <int R>
-  __device__ __forceinline__ bool iter() {
+  __device__ __forceinline__ void accumulate(const P* buf, P my_rho, P my_psi, P my_drho, P& Sx0,
+                                             P& Sy0, P& Cx0, P& Cy0, P& drho0, P& psi0) {
     constexpr int k0 = R % 5, k1 = (R + 1) % 5, k2 = (R + 2) % 5, k3 = (R + 3) % 5,
                   k4 = (R + 4) % 5;
-    if (!mbar_wait_bounded(&bars[slot], (uint32_t)parity)) {
-      atomicExch(&status->timeout, 1u);
-      *s_abort = 1;
-    }
-    const T2* srow = stage + slot * SLOT;
-    P* rbuf = rowbuf0 + (q & 1) * 2 * EXT;  // [0, EXT): rho pairs; [EXT, 2 EXT): psi pairs
-    // ---- density and pseudo-potential pair of this thread's column ----
-    P my_rho = pbc(C(0)), my_psi = pbc(C(0)), my_drho = pbc(C(0));
-    if (ecol >= 0) {
-      const T2* p = srow + (ecol - 2 + SOFF);
-      P a = PS::ld(p[0]);
-#pragma unroll
-      for (int i = 1; i < 9; ++i) a = padd(a, PS::ld(p[i * SW]));
-      my_drho = a;
-      my_rho = padd(rho_ref, a);
-      const P ex = pmk(exp_c<C>(-a.x * ph.inv_rho0), exp_c<C>(-a.y * ph.inv_rho0));
-      my_psi = pfma(mrho0E, ex, pbc(ph.rho0));
-      rbuf[ecol] = my_rho;
-      rbuf[EXT + ecol] = my_psi;
-    }
-    __syncthreads();
-    if (*s_abort) return false;
-    // every thread has finished row q-1, so the slot of row q-3 is free
-    if (producer && issued < nstage) {
-      const int rp = ring + issued;
-      issue_row<STORAGE>(src, stage + (rp % NSLOT) * SLOT, &bars[rp % NSLOT], g, x0,
-                         ylo - 2 + issued, lane);
-      ++issued;
-    }
+    const int e = lane + 2;
+    const P* pp = buf + WEXT;
+    const P m2 = pp[e - 2], m1 = pp[e - 1], p1 = pp[e + 1], p2 = pp[e + 2];
+    const P D1 = psub(p1, m1), D2 = psub(p2, m2), P1 = padd(p1, m1), P2 = padd(p2, m2);
+    const P T0 = pfma(Wa, D1, pmul(W2c, D2));
+    const P T1 = pfma(Wb, D1, pmul(W2d, D2));
+    const P T2v = pfma(Wd, D1, pmul(W2e, D2));
+    const P H1 = pfma(Wa, my_psi, pfma(Wb, P1, pmul(Wd, P2)));
+    const P H2 = pfma(Wc, my_psi, pfma(Wd, P1, pmul(We, P2)));
+    Sx[k0] = padd(Sx[k0], T2v);
+    Sx[k1] = padd(Sx[k1], T1);
+    Sx[k2] = padd(Sx[k2], T0);
+    Sx[k3] = padd(Sx[k3], T1);
+    Sx[k4] = T2v;
+    Sy[k0] = pfma(pbc(C(2)), H2, Sy[k0]);
+    Sy[k1] = padd(Sy[k1], H1);
+    Sy[k3] = psub(Sy[k3], H1);
+    Sy[k4] = pmul(pbc(C(-2)), H2);
+    // inter-species term: the other species' density (the swapped pair) on belt 1
+    const P rm1 = buf[e - 1], rp1 = buf[e + 1];
+    const P E1 = pswap(psub(rp1, rm1)), Q1 = pswap(padd(rp1, rm1));
+    const P X0 = pmul(pbc(ph.gw[0]), E1), X1 = pmul(pbc(ph.gw[1]), E1);
+    const P K = pfma(pbc(ph.gw[0]), pswap(my_rho), pmul(pbc(ph.gw[1]), Q1));
+    Cx[k1] = padd(Cx[k1], X1);
+    Cx[k2] = padd(Cx[k2], X0);
+    Cx[k3] = X1;
+    Cy[k1] = padd(Cy[k1], K);
+    Cy[k3] = psub(pbc(C(0)), K);
+    lag_drho[k2] = my_drho;
+    lag_psi[k2] = my_psi;
+    Sx0 = Sx[k0];
+    Sy0 = Sy[k0];
+    Cx0 = Cx[k0];
+    Cy0 = Cy[k0];
+    drho0 = lag_drho[k0];
+    psi0 = lag_psi[k0];
+  }
 
-    if (compute) {
-      const int e = ecol;
-      // ---- this row's contribution to the force stencil of rows r-2 .. r+2 ----
-      {
-        const P* pp = rbuf + EXT;
-        const P m2 = pp[e - 2], m1 = pp[e - 1], p1 = pp[e + 1], p2 = pp[e + 2];
-        const P D1 = psub(p1, m1), D2 = psub(p2, m2), P1 = padd(p1, m1), P2 = padd(p2, m2);
-        const P T0 = pfma(Wa, D1, pmul(W2c, D2));
-        const P T1 = pfma(Wb, D1, pmul(W2d, D2));
-        const P T2v = pfma(Wd, D1, pmul(W2e, D2));
-        const P H1 = pfma(Wa, my_psi, pfma(Wb, P1, pmul(Wd, P2)));
-        const P H2 = pfma(Wc, my_psi, pfma(Wd, P1, pmul(We, P2)));
-        Sx[k0] = padd(Sx[k0], T2v);
-        Sx[k1] = padd(Sx[k1], T1);
-        Sx[k2] = padd(Sx[k2], T0);
-        Sx[k3] = padd(Sx[k3], T1);
-        Sx[k4] = T2v;
-        Sy[k0] = pfma(pbc(C(2)), H2, Sy[k0]);
-        Sy[k1] = padd(Sy[k1], H1);
-        Sy[k3] = psub(Sy[k3], H1);
-        Sy[k4] = pmul(pbc(C(-2)), H2);
-        // inter-species term: the other species' density (the swapped pair) on belt 1
-        const P* ro = rbuf;
-        const P rm1 = ro[e - 1], rp1 = ro[e + 1];
-        const P E1 = pswap(psub(rp1, rm1)), Q1 = pswap(padd(rp1, rm1));
-        const P X0 = pmul(pbc(ph.gw[0]), E1), X1 = pmul(pbc(ph.gw[1]), E1);
-        const P K = pfma(pbc(ph.gw[0]), pswap(my_rho), pmul(pbc(ph.gw[1]), Q1));
-        Cx[k1] = padd(Cx[k1], X1);
-        Cx[k2] = padd(Cx[k2], X0);
-        Cx[k3] = X1;
-        Cy[k1] = padd(Cy[k1], K);
-        Cy[k3] = psub(pbc(C(0)), K);
-        lag_drho[k2] = my_drho;
-        lag_psi[k2] = my_psi;
+  // sum of the eight moving populations as they will be stored (pairwise)
+  __device__ __forceinline__ P stored_sum8(const P (&d)[9]) const {
+    P v[9];
+#pragma unroll
+    for (int i = 1; i < 9; ++i) v[i] = PS::ld(PS::st(d[i]));
+    return padd(padd(padd(v[1], v[2]), padd(v[3], v[4])), padd(padd(v[5], v[6]), padd(v[7], v[8])));
+  }
+
+  // rho/psi of this thread's column and of one halo column (lanes 0..3 serve
+  // the warp's four halo columns, buffer entries 0, 1, 34, 35; the other
+  // lanes repeat those reads and drop the result, which keeps the code
+  // branch-free) of staged row j
+  struct RowVals {
+    P rho, psi, drho, hrho, hpsi;
+  };
+  __device__ __forceinline__ int halo_entry() const {
+    const int l = lane & 3;
+    return (l < 2) ? l : 32 + l;
+  }
+  __device__ __forceinline__ RowVals row_values(int j) const {
+    const T2* srow = sm.stage + slot_of(j) * SLOT;
+    RowVals v;
+    P hd;
+    column(srow, SOFF + t, v.rho, v.psi, v.drho);
+    column(srow, SOFF + warp * 32 - 2 + halo_entry(), v.hrho, v.hpsi, hd);
+    return v;
+  }
+
+  __device__ __forceinline__ bool wait_row(int j) {
+    if (!mbar_wait_bounded(&sm.full[slot_of(j)], round_of(j) & 1)) {
+      if (lane == 0) {
+        atomicExch(&status->timeout, 1u);
+        *s_abort = 1;
       }
-      // ---- row o = r - 2 is complete: collide and push ----
-      if (q >= 4 && active) collide(ylo + q - 4, Sx[k0], Sy[k0], Cx[k0], Cy[k0], lag_drho[k0],
-                                    lag_psi[k0]);
+      return false;
     }
-    if (++slot == NSLOT) {
-      slot = 0;
-      parity ^= 1;
+    return *(volatile int*)s_abort == 0;
+  }
+
+  // One staged row q.  On entry `cur` holds rho/psi of row q; the values of
+  // row q+1 are formed together with the collision of row q-2 (independent
+  // work that fills each other's latency).  COLLIDE: q >= 4.
+  template <bool COLLIDE>
+  __device__ __forceinline__ bool iter(int q, int R, RowVals& cur) {
+    // the warp's row buffer: every lane has read row q-1's values
+    __syncwarp();
+    wbuf[lane + 2] = cur.rho;
+    wbuf[WEXT + lane + 2] = cur.psi;
+    if (lane < 4) {
+      wbuf[halo_entry()] = cur.hrho;
+      wbuf[WEXT + halo_entry()] = cur.hpsi;
     }
-    ++q;
+    __syncwarp();
+    P Sx0, Sy0, Cx0, Cy0, drho0, psi0;
+    switch (R) {
+      case 0: accumulate<0>(wbuf, cur.rho, cur.psi, cur.drho, Sx0, Sy0, Cx0, Cy0, drho0, psi0); break;
+      case 1: accumulate<1>(wbuf, cur.rho, cur.psi, cur.drho, Sx0, Sy0, Cx0, Cy0, drho0, psi0); break;
+      case 2: accumulate<2>(wbuf, cur.rho, cur.psi, cur.drho, Sx0, Sy0, Cx0, Cy0, drho0, psi0); break;
+      case 3: accumulate<3>(wbuf, cur.rho, cur.psi, cur.drho, Sx0, Sy0, Cx0, Cy0, drho0, psi0); break;
+      default: accumulate<4>(wbuf, cur.rho, cur.psi, cur.drho, Sx0, Sy0, Cx0, Cy0, drho0, psi0); break;
+    }
+    const bool more = q + 1 < nstage;
+    if (more && !wait_row(q + 1)) return false;
+    // (the last row re-reads its own slot instead of a next one)
+    const int jn = more ? q + 1 : q;
+    if (COLLIDE) {
+      // ---- row o = r - 2 (staged row q - 2) is complete: collide and push ----
+      P d[9], rho;
+      relax(sm.stage + slot_of(q - 2) * SLOT + SOFF + t, Sx0, Sy0, Cx0, Cy0, drho0, psi0, d, rho);
+      cur = row_values(jn);
+      if (active) push(ylo + q - 4, d, rho, drho0);
+    } else {
+      cur = row_values(jn);
+    }
+    if (q >= 2) {
+      // the warp is done with staged row q - 2
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sm.empty[slot_of(q - 2)]);
+    }
     return true;
   }
 
-  __device__ __forceinline__ void collide(int o, P Sx0, P Sy0, P Cx0, P Cy0, P drho, P psi0) {
-    const int oslot = slot >= 2 ? slot - 2 : slot + NSLOT - 2;
-    const T2* orow = stage + oslot * SLOT + t + SOFF;
-    P d[9];
+  // ---- a compute warp, without the pipelining (fewer live registers) ----
+  __device__ __forceinline__ void consume_plain() {
+    int R = 0;
+#pragma unroll 1
+    for (int q = 0; q < nstage; ++q) {
+      if (!wait_row(q)) return;
+      const RowVals cur = row_values(q);
+      __syncwarp();  // every lane has read row q-1's values
+      wbuf[lane + 2] = cur.rho;
+      wbuf[WEXT + lane + 2] = cur.psi;
+      if (lane < 4) {
+        wbuf[halo_entry()] = cur.hrho;
+        wbuf[WEXT + halo_entry()] = cur.hpsi;
+      }
+      __syncwarp();
+      P Sx0, Sy0, Cx0, Cy0, drho0, psi0;
+      switch (R) {
+        case 0: accumulate<0>(wbuf, cur.rho, cur.psi, cur.drho, Sx0, Sy0, Cx0, Cy0, drho0, psi0); break;
+        case 1: accumulate<1>(wbuf, cur.rho, cur.psi, cur.drho, Sx0, Sy0, Cx0, Cy0, drho0, psi0); break;
+        case 2: accumulate<2>(wbuf, cur.rho, cur.psi, cur.drho, Sx0, Sy0, Cx0, Cy0, drho0, psi0); break;
+        case 3: accumulate<3>(wbuf, cur.rho, cur.psi, cur.drho, Sx0, Sy0, Cx0, Cy0, drho0, psi0); break;
+        default: accumulate<4>(wbuf, cur.rho, cur.psi, cur.drho, Sx0, Sy0, Cx0, Cy0, drho0, psi0); break;
+      }
+      R = (R == 4) ? 0 : R + 1;
+      if (q >= 2) {
+        // ---- row o = r - 2 (staged row q - 2) is complete: collide and push ----
+        if (q >= 4 && active) {
+          P d[9], rho;
+          relax(sm.stage + slot_of(q - 2) * SLOT + SOFF + t, Sx0, Sy0, Cx0, Cy0, drho0, psi0, d,
+                rho);
+          push(ylo + q - 4, d, rho, drho0);
+        }
+        // the warp is done with staged row q - 2
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sm.empty[slot_of(q - 2)]);
+      }
+    }
+    // release the last two staged rows (halo rows, never collided)
+    __syncwarp();
+    if (lane == 0) {
+      for (int j = (nstage >= 2 ? nstage - 2 : 0); j < nstage; ++j) mbar_arrive(&sm.empty[slot_of(j)]);
+    }
+  }
+
+  // ---- a compute warp: rows 0 .. nstage-1 ----
+  __device__ __forceinline__ void consume() {
+    if (!RowsCfg<STORAGE>::PIPE) {
+      consume_plain();
+      return;
+    }
+    if (!wait_row(0)) return;
+    RowVals cur = row_values(0);
+    int q = 0, R = 0;
+#pragma unroll 1
+    for (; q < 4 && q < nstage; ++q) {
+      if (!iter<false>(q, R, cur)) return;
+      R = (R == 4) ? 0 : R + 1;
+    }
+#pragma unroll 1
+    for (; q < nstage; ++q) {
+      if (!iter<true>(q, R, cur)) return;
+      R = (R == 4) ? 0 : R + 1;
+    }
+    // release the last two staged rows (halo rows, never collided)
+    __syncwarp();
+    if (lane == 0) {
+      for (int j = (nstage >= 2 ? nstage - 2 : 0); j < nstage; ++j) mbar_arrive(&sm.empty[slot_of(j)]);
+    }
+  }
+
+  // The shifted-BGK collision of one site (populations re-read from the
+  // staged row): d[] becomes f*_i - w_i rho_ref (mass-exact rest population
+  // for the rounded storages); rho is the site's density pair.
+  __device__ __forceinline__ void relax(const T2* orow, P Sx0, P Sy0, P Cx0, P Cy0, P drho,
+                                        P psi0, P (&d)[9], P& rho_out) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) d[i] = PS::ld(orow[i * SW]);
     const P rho = padd(rho_ref, drho);
+    rho_out = rho;
     // G = -F: F_s = -psi_s S_s - rho_s C_s
     const P Gx = pfma(psi0, Sx0, pmul(rho, Cx0));
     const P Gy = pfma(psi0, Sy0, pmul(rho, Cy0));
@@ -381,11 +574,12 @@ struct RowsLoop {
       // mass-exact rest population: the collision conserves rho_s exactly,
       // so give the rest population what the eight moving ones (as stored)
       // leave of drho; one rounding per site instead of a biased sum of nine
-      P r8 = PS::ld(PS::st(d[1]));
-#pragma unroll
-      for (int i = 2; i < 9; ++i) r8 = padd(r8, PS::ld(PS::st(d[i])));
-      d[0] = psub(drho, r8);
+      d[0] = psub(drho, stored_sum8(d));
     }
+  }
+
+  // Push f*_i of site (o, x) to r + c_i (Ladd bounce-back at Couette walls).
+  __device__ __forceinline__ void push(int o, P (&d)[9], P rho, P drho) {
     // 16-bit storages round the rest population stochastically; the bits are
     // hashed from the site and its relaxed populations (deterministic runs)
     uint32_t rbits = 0;
@@ -420,12 +614,8 @@ struct RowsLoop {
           d[i] = pfma(pbc(-C(6) * wq<C>(i) * C(Q9::cx(i)) * Uw), rho, d[i]);
         }
       }
-      if (STORAGE != LB_F64) {  // mass-exact again, with the values the wall sends back
-        P r8 = PS::ld(PS::st(d[1]));
-#pragma unroll
-        for (int i = 2; i < 9; ++i) r8 = padd(r8, PS::ld(PS::st(d[i])));
-        d[0] = psub(drho, r8);
-      }
+      if (STORAGE != LB_F64)  // mass-exact again, with the values the wall sends back
+        d[0] = psub(drho, stored_sum8(d));
 #pragma unroll
       for (int i = 0; i < 9; ++i) {
         const int yd = o + Q9::cy(i);
@@ -439,65 +629,27 @@ struct RowsLoop {
     }
   }
 
-  // drain: wait (bounded) for the rows staged but not consumed, so that no
-  // copy is still writing into this CTA's shared memory when it exits
-  __device__ __forceinline__ void drain() {
-    if (!(producer && lane == 0)) return;
-    for (int k = q; k < issued; ++k) {
-      const int rp = ring + k;
-      const long long t0 = clock64();
-      while (!mbar_try_wait(&bars[rp % NSLOT], (uint32_t)((rp / NSLOT) & 1))) {
-        if (clock64() - t0 > (1LL << 31)) break;
-      }
-    }
-  }
 };
 
-// One CTA, one work range: columns x0 .. x0+RX-1 (clipped to nx), output rows
+// One CTA, one work range: columns x0 .. x1-1 (at most RX), output rows
 // ylo .. yhi-1 of the lattice (src -> dst).  `ring` is the position of the
 // next staged row in the CTA's slot ring (identical in every thread); on
-// entry every slot is free.  Returns false if a bounded wait gave up (after
-// draining the copies this range issued).
+// entry every slot is free or will be released by the compute warps.  A
+// bounded wait that gives up raises *s_abort (read it after a __syncthreads).
 template <int STORAGE>
-__device__ __forceinline__ bool rows_range(
+__device__ __forceinline__ void rows_range(
     const typename PairStore<STORAGE>::T2* __restrict__ src,
     typename PairStore<STORAGE>::T2* __restrict__ dst, const Geom& g,
-    const Phys<typename Store<STORAGE>::C>& ph, int x0, int ylo, int yhi,
-    typename PairStore<STORAGE>::T2* stage, typename PairOf<typename Store<STORAGE>::C>::P* rowbuf0,
-    uint64_t* bars, int& ring, int* s_abort, Status* status, int& bad) {
-  RowsLoop<STORAGE> L(src, dst, g, ph, x0, ylo, yhi, stage, rowbuf0, bars, ring, s_abort, status);
-  L.prologue();
-  bool ok = true;
-#pragma unroll 1
-  while (L.q < L.nstage) {
-    if (!(ok = L.template iter<0>()) || L.q >= L.nstage) break;
-    if (!(ok = L.template iter<1>()) || L.q >= L.nstage) break;
-    if (!(ok = L.template iter<2>()) || L.q >= L.nstage) break;
-    if (!(ok = L.template iter<3>()) || L.q >= L.nstage) break;
-    if (!(ok = L.template iter<4>())) break;
-  }
-  if (!ok) L.drain();
+    const Phys<typename Store<STORAGE>::C>& ph, int x0, int x1, int ylo, int yhi,
+    const RowsSmem<STORAGE>& sm, int& ring, int* s_abort, Status* status, int& bad) {
+  RowsLoop<STORAGE> L(src, dst, g, ph, x0, x1, ylo, yhi, sm, ring, s_abort, status);
+  if (L.warp == NCW)
+    L.produce();
+  else
+    L.consume();
   bad += L.bad;
   ring += L.nstage;
-  return ok;
 }
-
-template <int STORAGE>
-struct RowsSmem {
-  using T2 = typename PairStore<STORAGE>::T2;
-  using P = typename PairOf<typename Store<STORAGE>::C>::P;
-  T2* stage;
-  P* rowbuf0;
-  uint64_t* bars;
-  __device__ __forceinline__ explicit RowsSmem(unsigned char* smem) {
-    constexpr int SLOT = 9 * stage_width<STORAGE>();
-    constexpr int NSLOT = RowsCfg<STORAGE>::NSLOT;
-    stage = reinterpret_cast<T2*>(smem);
-    rowbuf0 = reinterpret_cast<P*>(smem + (size_t)NSLOT * SLOT * sizeof(T2));
-    bars = reinterpret_cast<uint64_t*>(smem + (size_t)NSLOT * SLOT * sizeof(T2) +
-                                       2 * 2 * (RX + 4) * sizeof(P));
-  }
-};
 
 // Single lattice: CTA b owns strip b % nstrips and row range b / nstrips.
 template <int STORAGE>
@@ -510,18 +662,18 @@ __global__ void __launch_bounds__(RTHREADS, RowsCfg<STORAGE>::MINB)
   RowsSmem<STORAGE> sm(smem);
   const int strip = blockIdx.x % nstrips;
   const int range = blockIdx.x / nstrips;
+  const int x0 = rows_strip_x0(strip, nstrips, g.nx);
+  const int x1 = rows_strip_x0(strip + 1, nstrips, g.nx);
   const int ylo = (int)((long long)range * g.ny / kranges);
   const int yhi = (int)((long long)(range + 1) * g.ny / kranges);
   if (yhi <= ylo) return;
   if (threadIdx.x == 0) {
-    for (int k = 0; k < RowsCfg<STORAGE>::NSLOT; ++k) mbar_init(&sm.bars[k], 1);
-    mbar_fence_init();
+    sm.init();
     s_abort = 0;
   }
   __syncthreads();
   int ring = 0, bad = 0;
-  rows_range<STORAGE>(src, dst, g, ph, strip * RX, ylo, yhi, sm.stage, sm.rowbuf0, sm.bars, ring,
-                      &s_abort, status, bad);
+  rows_range<STORAGE>(src, dst, g, ph, x0, x1, ylo, yhi, sm, ring, &s_abort, status, bad);
   if (bad) atomicAdd(&status->bad_rho, (unsigned)bad);
 }
 
@@ -547,8 +699,7 @@ __global__ void __launch_bounds__(RTHREADS, RowsCfg<STORAGE>::MINB)
   __shared__ T2* s_dst;
   RowsSmem<STORAGE> sm(smem);
   if (threadIdx.x == 0) {
-    for (int k = 0; k < RowsCfg<STORAGE>::NSLOT; ++k) mbar_init(&sm.bars[k], 1);
-    mbar_fence_init();
+    sm.init();
     s_abort = 0;
   }
   int ring = 0, bad = 0;
@@ -566,10 +717,10 @@ __global__ void __launch_bounds__(RTHREADS, RowsCfg<STORAGE>::MINB)
     }
     __syncthreads();
     if (s_skip) continue;
-    if (!rows_range<STORAGE>(s_src, s_dst, s_g, s_ph, s_item.x0, s_item.ylo, s_item.yhi, sm.stage,
-                             sm.rowbuf0, sm.bars, ring, &s_abort, status, bad))
-      break;
+    rows_range<STORAGE>(s_src, s_dst, s_g, s_ph, s_item.x0, s_item.x1, s_item.ylo, s_item.yhi, sm,
+                        ring, &s_abort, status, bad);
     __syncthreads();
+    if (s_abort) break;
     if (threadIdx.x == 0) {
       ReplicaDev<C>& R = reps[s_item.replica];
       const unsigned prev = atomicAdd(&R.done, 1u);
@@ -619,7 +770,10 @@ static int resident(int storage, bool batch) {
   return 0;
 }
 
-int rows_strip_width() { return RX; }
+int rows_strip_width() {
+  static_assert(RX == 128, "rows_strip_x0 assumes 128-column strips");
+  return RX;
+}
 
 bool rows_geometry_ok(const Geom& g, int storage) {
   const int pair_bytes = 2 * (int)elem_size(storage);
@@ -642,7 +796,7 @@ template <int STORAGE>
 static cudaError_t rows_t(const void* src, void* dst, const Geom& g, const PhysD& pd,
                           Status* status, cudaStream_t st) {
   using T2 = typename PairStore<STORAGE>::T2;
-  const int nstrips = (g.nx + RX - 1) / RX;
+  const int nstrips = rows_nstrips(g.nx);
   int k = resident(STORAGE, false) / nstrips;
   if (k < 1) k = 1;
   if (k > g.ny) k = g.ny;

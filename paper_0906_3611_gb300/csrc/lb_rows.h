@@ -18,13 +18,19 @@ struct ReplicaDev {
   unsigned int done;   // items finished in the current step
 };
 
-// One work item: strip starting at column x0, output rows [ylo, yhi).
+// One work item: strip columns [x0, x1), output rows [ylo, yhi).
 struct WorkItem {
-  int replica, x0, ylo, yhi;
+  int replica, x0, x1, ylo, yhi;
 };
 
 // Columns per strip of the row-streaming kernels.
 int rows_strip_width();
+
+// Strips of a lattice row: 128 columns (the last one ragged).
+__host__ __device__ inline int rows_nstrips(int nx) { return (nx + 127) / 128; }
+__host__ __device__ inline int rows_strip_x0(int j, int nstrips, int nx) {
+  return j >= nstrips ? nx : j * 128;
+}
 
 // True if the row-streaming kernel handles this lattice shape and storage.
 bool rows_geometry_ok(const Geom& g, int storage);
