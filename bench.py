@@ -125,6 +125,64 @@ def dist_env():
     return rank, world, local
 
 
+class Dist:
+    """One process per GPU under torchrun.  The path does not shard: every rank
+    runs its own replica(s), and the only collectives are the barriers around
+    the timed region and the reductions of the results below (NCCL on GPUs;
+    gloo with device "cpu" in the CPU tests)."""
+
+    def __init__(self, backend: str = "nccl", device: str = "cuda"):
+        self.rank, self.world, self.local = dist_env()
+        self.device = device
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.device == "cuda":
+            import torch
+            torch.cuda.synchronize()
+        if self.pg is not None:
+            self.pg.barrier()
+        if self.device == "cuda":
+            import torch
+            torch.cuda.synchronize()
+
+    def _reduce(self, x: float, op: str) -> float:
+        if self.pg is None:
+            return float(x)
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.pg.all_reduce(t, op=getattr(self.pg.ReduceOp, op))
+        return float(t.item())
+
+    def max(self, x: float) -> float:
+        return self._reduce(x, "MAX")
+
+    def sum(self, x: float) -> float:
+        return self._reduce(x, "SUM")
+
+    def gather(self, xs: list) -> list:
+        """Concatenation of every rank's list (rank order)."""
+        if self.pg is None:
+            return list(xs)
+        out = [None] * self.world
+        self.pg.all_gather_object(out, list(xs))
+        return [v for part in out for v in part]
+
+    def close(self):
+        if self.pg is not None:
+            self.pg.destroy_process_group()
+            self.pg = None
+
+
+def whole_job_mlups(site_updates_all_ranks: float, seconds_slowest_rank: float) -> float:
+    """Whole-job throughput: every rank's site updates over the slowest rank's time."""
+    return site_updates_all_ranks / seconds_slowest_rank / 1e6
+
+
 def cpu_baseline_run(nx, ny, boundary, U, steps):
     """Time the FP64 oracle (as it stands) on the host cores."""
     import oracle
@@ -176,11 +234,7 @@ def run_gpu(args):
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
-    pg = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-        pg = dist
+    D = Dist()
     nx, ny, boundary, U, storage = WORKLOADS[args.workload]
     params = lb.make_params(**PHYS, boundary=boundary, U_wall=U, storage=storage,
                             rho_ref=(0.87, 0.43), init_kind=lb.LB_INIT_BERNOULLI, init=INIT)
@@ -189,11 +243,7 @@ def run_gpu(args):
     lat.init_random(rank)
     sites = nx * ny
 
-    def barrier():
-        torch.cuda.synchronize()
-        if pg is not None:
-            pg.barrier()
-        torch.cuda.synchronize()
+    barrier = D.barrier
 
     sampler = ClockSampler(torch.cuda.current_device() if world == 1 else local)
     sampler.start()
@@ -210,11 +260,8 @@ def run_gpu(args):
     clocks = sampler.stop()
     ms = start.elapsed_time(end)
     status = lat.status()
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if pg is not None:
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * sites * args.steps / (ms_max * 1e-3) / 1e6
+    ms_max = D.max(ms)
+    value = whole_job_mlups(D.sum(sites * args.steps), ms_max * 1e-3)
 
     # end-to-end through the C ABI with host buffers: pinned host state -> device,
     # K steps, FP64 observables back to the host
@@ -229,10 +276,7 @@ def run_gpu(args):
     lb.lb_step(lat.h, args.steps)
     lb.lb_observables(lat.h, None, None, stress, mass)
     e2e_s = time.perf_counter() - t0
-    t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if pg is not None:
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-    e2e_value = world * sites * args.steps / float(t.item()) / 1e6
+    e2e_value = whole_job_mlups(D.sum(sites * args.steps), D.max(e2e_s))
 
     bytes_per_site = 2 * 18 * es  # 18 populations read + 18 written
     kernel_s = ms * 1e-3 / args.steps
@@ -278,8 +322,7 @@ def run_gpu(args):
                 "impl": "gb300"}
         print(json.dumps(line), flush=True)
     lat.close()
-    if pg is not None:
-        pg.destroy_process_group()
+    D.close()
 
 
 def batch_replicas(name):
@@ -302,6 +345,7 @@ def run_batch(args):
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    D = Dist()
     reps, storage = batch_replicas(args.workload)
     stream = torch.cuda.Stream()
 
@@ -321,18 +365,21 @@ def run_batch(args):
     sampler.start()
     b.run(args.warmup)
     stream.synchronize()
+    D.barrier()
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
     start.record(stream)
     b.run(args.steps)
     end.record(stream)
     end.synchronize()
+    D.barrier()
     clocks = sampler.stop()
     ms = start.elapsed_time(end)
     rem, done = b.poll()
     status = b.status()
     b.close()
-    value = sites * args.steps / (ms * 1e-3) / 1e6
+    ms_max = D.max(ms)
+    value = whole_job_mlups(D.sum(sites * args.steps), ms_max * 1e-3)
 
     # the same replicas, one lattice at a time (each replica's steps in one lb_step)
     seq_steps = max(1, args.steps // 4)
@@ -350,14 +397,14 @@ def run_batch(args):
         s1.synchronize()
         t_seq += s0.elapsed_time(s1)
         lat.close()
-    seq_value = sites * seq_steps / (t_seq * 1e-3) / 1e6
+    seq_value = whole_job_mlups(D.sum(sites * seq_steps), D.max(t_seq) * 1e-3)
     es = ELEM[storage]
     bytes_per_site = 2 * 18 * es
     achieved = bytes_per_site * sites / (ms * 1e-3 / args.steps) / 1e9
     peak, peak_kind = peaks()
     if rank == 0:
         line = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic",
                 "config": {"workload": args.workload, "replicas": len(reps), "sites": sites,
@@ -372,6 +419,7 @@ def run_batch(args):
                 "gpu_launches": args.steps, "clocks": clocks,
                 "status": lb.lb_strerror(status), "impl": "gb300"}
         print(json.dumps(line), flush=True)
+    D.close()
 
 
 def run_serve(args):
@@ -383,6 +431,7 @@ def run_serve(args):
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    D = Dist()
     storage, n, rate, sides, steps_range, budget, slots, chunk = SERVES[args.workload]
     if args.requests:
         n = args.requests
@@ -391,32 +440,39 @@ def run_serve(args):
     srv = serve.Server(PHYS, storage, capacity=slots, chunk=chunk, budget_bytes=budget)
     sampler = ClockSampler(local)
     sampler.start()
+    D.barrier()
     t0 = time.perf_counter()
     res = srv.run(reqs)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
+    D.barrier()
     clocks = sampler.stop()
     srv.close()
-    lat = np.array([r.latency for r in res])
-    done_updates = sum(r.side * r.side * r.steps for r in res)
-    value = done_updates / wall / 1e6
-    span = max(r.arrival for r in reqs)
+    lat = np.array(D.gather([r.latency for r in res]))
+    done_updates = D.sum(sum(r.side * r.side * r.steps for r in res))
+    wall = D.max(wall)
+    value = whole_job_mlups(done_updates, wall)
+    offered = D.sum(offered)
+    completed = int(D.sum(len(res)))
+    span = D.max(max(r.arrival for r in reqs))
+    steps_done = int(D.sum(sum(r.steps for r in res)))
     if rank == 0:
         line = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
-                "steps": int(sum(r.steps for r in res)), "warmup": 0,
+                "steps": steps_done, "warmup": 0,
                 "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": args.workload, "requests": n, "arrival_rate_per_s": rate,
                            "sides": f"uniform {sides[0]}..{sides[-1]} step 64",
                            "steps": "log-uniform [1e3, 1e5]", "hbm_budget_gb": budget / 1e9,
                            "slots": slots, "chunk_steps": chunk, "storage": STORAGE_NAME[storage]},
-                "served": {"completed": len(res), "wall_s": wall,
+                "served": {"completed": completed, "wall_s": wall,
                            "latency_p50_s": float(np.percentile(lat, 50)),
                            "latency_p99_s": float(np.percentile(lat, 99)),
                            "offered_mlups": offered / max(span, 1e-9) / 1e6,
                            "overload_factor": (offered / max(span, 1e-9)) / (done_updates / wall)},
                 "clocks": clocks, "impl": "gb300"}
         print(json.dumps(line), flush=True)
+    D.close()
 
 
 def main():
