@@ -358,7 +358,7 @@ def run_batch(args):
     budget = args.warmup + args.steps + 64
     for side, U, seed in reps:
         b.add(side, side, prm(U), seed, budget)
-    rows = b.autotune(2)
+    layout, rows = b.autotune(2)
     for k in range(len(reps)):  # the autotuner spent budget: refill it
         b.set_steps(k, args.warmup + args.steps)
     sampler = ClockSampler(local)
@@ -410,7 +410,9 @@ def run_batch(args):
                 "config": {"workload": args.workload, "replicas": len(reps), "sites": sites,
                            "sides": sorted(set(s for s, _, _ in reps)),
                            "storage": STORAGE_NAME[storage], "boundary": "couette",
-                           "U_wall": "uniform[0, 0.05]", "rows_per_item": rows,
+                           "U_wall": "uniform[0, 0.05]",
+                           "work_list": {"layout": ["contiguous", "packed"][layout],
+                                         "max_piece_rows": rows},
                            "l2": f"inputs larger than L2 ({sites * 18 * es / 1e9:.1f} GB per buffer set)"},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": None,

@@ -227,7 +227,10 @@ LB_API int lb_batch_create(int capacity, int storage, void *cuda_stream, lb_batc
 
 /* Add a replica: allocates its two population buffers, fills them with the
  * seeded recipe of p (as lb_init_random), and gives it `steps` steps of
- * budget.  *slot receives its slot.  LB_EBUSY when every slot is taken. */
+ * budget.  *slot receives its slot.  LB_EBUSY when every slot is taken, or
+ * when p would be the 17th distinct physics set of the batch (couplings,
+ * tau, rho0, rho_ref; the wall speed U may differ freely): a launch carries
+ * at most 16 sets in its parameters. */
 LB_API int lb_batch_add(lb_batch *b, int nx, int ny, const lb_params *p, uint64_t seed,
                         int64_t steps, int *slot);
 
@@ -250,11 +253,16 @@ LB_API int lb_batch_observables(lb_batch *b, int slot, double *rho, double *u, d
                                 double *mass);
 LB_API int lb_batch_get_state(lb_batch *b, int slot, double *f);
 
-/* Pick the rows per work item (16 ... 256) that time fastest on the current
- * replicas; each candidate runs steps_per_candidate + 1 real steps of every
- * replica with budget left (spending that budget).  *rows_per_item receives
- * the choice (may be NULL). */
-LB_API int lb_batch_autotune(lb_batch *b, int steps_per_candidate, int *rows_per_item);
+/* Pick the work-list layout and piece length that time fastest on the
+ * current replicas, among five candidates: layout 0 deals the strip-rows of
+ * all replicas out to the CTAs in contiguous equal shares (balanced whatever
+ * the sizes); layout 1 cuts every replica into strips x equal row ranges and
+ * packs them into the CTAs (neighbouring strips advance together and share
+ * halos through L2); each uncut or with ranges cut at 512 or 128 rows.  Each
+ * candidate runs steps_per_candidate + 1 real steps of every replica with
+ * budget left (spending that budget).  *layout and *rows_per_item receive the
+ * choice (either may be NULL); the batch keeps it until the next call. */
+LB_API int lb_batch_autotune(lb_batch *b, int steps_per_candidate, int *layout, int *rows_per_item);
 
 /* Read and clear the batch's device status word (as lb_status). */
 LB_API int lb_batch_status(lb_batch *b);

@@ -7,7 +7,11 @@
 #include <stddef.h>
 #include <string.h>
 
+#include <algorithm>
+#include <functional>
 #include <new>
+#include <queue>
+#include <utility>
 #include <vector>
 
 #include "lb.h"
@@ -41,7 +45,7 @@ struct lb_batch {
   void* d_reps = nullptr;            // capacity ReplicaDev records
   WorkItem* d_items = nullptr;
   int items_cap = 0;
-  int* d_nitems = nullptr;
+  int* d_offsets = nullptr;          // grid + 1: CTA c works on items [off[c], off[c+1])
   int n_items = 0;
   Status* d_status = nullptr;
   double* d_partials = nullptr;
@@ -50,9 +54,14 @@ struct lb_batch {
   double* h_out = nullptr;
   double* d_stage = nullptr;
   size_t stage_bytes = 0;
-  int rows_per_item = 64;
+  int layout = 0;                    // work-list layout (autotuned): 0 contiguous, 1 packed
+  int rows_per_item = 1 << 30;       // longest piece (autotuned); default: no cut
   int grid = 0;
   bool dirty = true;
+  // distinct physics sets (couplings, tau, rho0, rho_ref) of the replicas,
+  // handed to every launch as a PhysTable<float> or PhysTable<double>
+  alignas(16) unsigned char table[sizeof(PhysTable<double>)] = {};
+  int nphys = 0;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
 };
@@ -79,12 +88,30 @@ static void fill_physd(const lb_params& p, PhysD* d) {
                          p.rho_ref);
 }
 
+static void drop_graph(lb_batch* b);
+
+// Index of the replica's physics set in the batch's table (added if new);
+// -1 when the table is full.
 template <typename C>
-static ReplicaDev<C> make_record(const Slot& s, int64_t steps) {
+static int phys_index(lb_batch* b, const PhysD& pd) {
+  Phys<C> p = make_phys<C>(pd);
+  p.Uwall = C(0);  // per replica, not part of a set
+  PhysTable<C>* tab = reinterpret_cast<PhysTable<C>*>(b->table);
+  for (int i = 0; i < b->nphys; ++i)
+    if (memcmp(&tab->p[i], &p, sizeof(p)) == 0) return i;
+  if (b->nphys == kMaxPhysSets) return -1;
+  tab->p[b->nphys] = p;
+  drop_graph(b);  // the captured launches carry the old table
+  return b->nphys++;
+}
+
+template <typename C>
+static ReplicaDev<C> make_record(const Slot& s, int phys, int64_t steps) {
   ReplicaDev<C> r;
   memset(&r, 0, sizeof(r));
   r.g = s.g;
-  r.ph = make_phys<C>(s.ph);
+  r.phys = phys;
+  r.Uwall = (C)s.ph.U;
   r.buf[0] = s.buf[0];
   r.buf[1] = s.buf[1];
   r.nitems = 0;
@@ -113,28 +140,140 @@ static void drop_graph(lb_batch* b) {
   }
 }
 
-// Work list: per used slot, row ranges of about rows_per_item rows (range-
-// major, strip-minor, so that concurrently running CTAs work on neighbouring
-// strips of the same rows and share halos through L2).
-static int rebuild_items(lb_batch* b) {
-  std::vector<WorkItem> items;
-  std::vector<int> counts(b->capacity, 0);
+// Work list, packed layout.  Each used replica is cut into pieces: its 128-column strips
+// times k row ranges of at most h rows (and at most rows_per_item, the
+// autotuned granularity).  The pieces are packed, largest first, into bins
+// of h + 4 staged rows (a range also stages 2+2 halo rows), and bin c is the
+// work of CTA c of the persistent grid; h is the smallest height for which
+// the bins fit the grid, so that the CTAs finish together.  A large replica's
+// pieces fill consecutive bins range-major: neighbouring CTAs stage the same
+// rows of neighbouring strips at the same time and share the halo columns and
+// the boundary sectors of their stores through L2 (strip-major chunks read
+// ~30 % more from DRAM).
+static void build_packed(lb_batch* b, std::vector<WorkItem>& items, std::vector<int>& offsets,
+                         std::vector<int>& counts) {
+  struct Piece {
+    long long w;  // staged rows: range rows + 4
+    WorkItem it;
+  };
+  int max_ny = 1;
+  for (int k = 0; k < b->capacity; ++k)
+    if (b->slots[k].used && b->slots[k].ny > max_ny) max_ny = b->slots[k].ny;
+  auto make_pieces = [&](long long h, std::vector<Piece>& pieces) {
+    pieces.clear();
+    std::fill(counts.begin(), counts.end(), 0);
+    const long long hmax = std::min<long long>(h, b->rows_per_item);
+    for (int k = 0; k < b->capacity; ++k) {
+      const Slot& s = b->slots[k];
+      if (!s.used) continue;
+      const int nstrips = rows_nstrips(s.nx);
+      long long kr = (s.ny + hmax - 1) / hmax;
+      if (kr > s.ny) kr = s.ny;
+      for (long long q = 0; q < kr; ++q) {
+        const int ylo = (int)(q * s.ny / kr), yhi = (int)((q + 1) * s.ny / kr);
+        for (int j = 0; j < nstrips; ++j) {
+          pieces.push_back(Piece{yhi - ylo + 4, WorkItem{k, rows_strip_x0(j, nstrips, s.nx),
+                                                         rows_strip_x0(j + 1, nstrips, s.nx),
+                                                         ylo, yhi}});
+          ++counts[k];
+        }
+      }
+    }
+    std::stable_sort(pieces.begin(), pieces.end(),
+                     [](const Piece& a, const Piece& c) { return a.w > c.w; });
+  };
+  // first-fit decreasing into bins of h + 4 staged rows; returns the bin count
+  // (stops counting past the grid unless `fill` receives the bins)
+  auto pack = [&](long long h, const std::vector<Piece>& pieces,
+                  std::vector<std::vector<WorkItem>>* fill) {
+    std::vector<long long> load;
+    for (const Piece& p : pieces) {
+      size_t i = 0;
+      while (i < load.size() && load[i] + p.w > h + 4) ++i;
+      if (i == load.size()) {
+        if (!fill && (int)load.size() >= b->grid) return (int)load.size() + 1;
+        load.push_back(0);
+        if (fill) fill->emplace_back();
+      }
+      load[i] += p.w;
+      if (fill) (*fill)[i].push_back(p.it);
+    }
+    return (int)load.size();
+  };
+  std::vector<Piece> pieces;
+  long long lo = 1, hi = max_ny;
+  make_pieces(hi, pieces);
+  while (pack(hi, pieces, nullptr) > b->grid) {  // many small replicas: bins hold several
+    hi *= 2;
+    make_pieces(hi, pieces);
+  }
+  while (lo < hi) {
+    const long long mid = (lo + hi) / 2;
+    make_pieces(mid, pieces);
+    if (pack(mid, pieces, nullptr) <= b->grid)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  make_pieces(hi, pieces);
+  std::vector<std::vector<WorkItem>> bins;
+  pack(hi, pieces, &bins);
+  for (int c = 0; c < b->grid; ++c) {
+    offsets[c] = (int)items.size();
+    if (c < (int)bins.size()) items.insert(items.end(), bins[c].begin(), bins[c].end());
+  }
+  offsets[b->grid] = (int)items.size();
+}
+// Work list, contiguous layout.  Every 128-column strip of every used replica
+// is a column of ny rows; these strip-rows are dealt out in order to the CTAs
+// of the persistent grid, W/G each (cut at rows_per_item), so that the CTAs
+// finish together whatever the replica sizes; a CTA streams long row ranges
+// and pays the pipeline fill and the 2+2 halo rows only at the one or two
+// range boundaries it owns.  Neighbouring strips are at different rows at a
+// given time, so their halo columns come from DRAM twice.
+static void build_contiguous(lb_batch* b, std::vector<WorkItem>& items, std::vector<int>& offsets,
+                             std::vector<int>& counts) {
+  long long total = 0;
+  for (int k = 0; k < b->capacity; ++k)
+    if (b->slots[k].used) total += (long long)rows_nstrips(b->slots[k].nx) * b->slots[k].ny;
+  const long long per = total > 0 ? (total + b->grid - 1) / b->grid : 1;
+  int cta = 0;
+  long long left = per;
   for (int k = 0; k < b->capacity; ++k) {
     const Slot& s = b->slots[k];
     if (!s.used) continue;
     const int nstrips = rows_nstrips(s.nx);
-    int nranges = (s.ny + b->rows_per_item / 2) / b->rows_per_item;
-    if (nranges < 1) nranges = 1;
-    for (int r = 0; r < nranges; ++r) {
-      const int ylo = (int)((long long)r * s.ny / nranges);
-      const int yhi = (int)((long long)(r + 1) * s.ny / nranges);
-      for (int j = 0; j < nstrips; ++j) {
-        items.push_back(WorkItem{k, rows_strip_x0(j, nstrips, s.nx),
-                                 rows_strip_x0(j + 1, nstrips, s.nx), ylo, yhi});
+    for (int j = 0; j < nstrips; ++j) {
+      const int x0 = rows_strip_x0(j, nstrips, s.nx), x1 = rows_strip_x0(j + 1, nstrips, s.nx);
+      int y = 0;
+      while (y < s.ny) {
+        long long take = std::min<long long>(std::min<long long>(s.ny - y, left), b->rows_per_item);
+        items.push_back(WorkItem{k, x0, x1, y, y + (int)take});
         ++counts[k];
+        y += (int)take;
+        left -= take;
+        if (left == 0) {  // this CTA's share is full: the next CTA takes over
+          if (cta < b->grid - 1) {
+            offsets[++cta] = (int)items.size();
+            left = per;
+          } else {
+            left = total;  // (cannot happen: grid * per >= total)
+          }
+        }
       }
     }
   }
+  for (int c = cta + 1; c <= b->grid; ++c) offsets[c] = (int)items.size();
+}
+
+static int rebuild_items(lb_batch* b) {
+  std::vector<WorkItem> items;
+  std::vector<int> offsets(b->grid + 1, 0);
+  std::vector<int> counts(b->capacity, 0);
+  if (b->layout == 1)
+    build_packed(b, items, offsets, counts);
+  else
+    build_contiguous(b, items, offsets, counts);
   // the per-replica item counts, one strided copy into the records
   if (cudaMemcpy2DAsync((char*)b->d_reps + field_off(b, 0), rep_bytes(b->storage), counts.data(),
                         sizeof(int), sizeof(int), (size_t)b->capacity, cudaMemcpyHostToDevice,
@@ -157,8 +296,8 @@ static int rebuild_items(lb_batch* b) {
       cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(WorkItem),
                       cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
     return LB_ECUDA;
-  if (cudaMemcpyAsync(b->d_nitems, &b->n_items, sizeof(int), cudaMemcpyHostToDevice, b->stream) !=
-      cudaSuccess)
+  if (cudaMemcpyAsync(b->d_offsets, offsets.data(), offsets.size() * sizeof(int),
+                      cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
     return LB_ECUDA;
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return LB_ECUDA;
   b->dirty = false;
@@ -186,7 +325,7 @@ extern "C" int lb_batch_create(int capacity, int storage, void* cuda_stream, lb_
   }
   b->grid = rows_batch_grid(storage);
   if (cudaMalloc(&b->d_reps, (size_t)capacity * rep_bytes(storage)) != cudaSuccess ||
-      cudaMalloc(&b->d_nitems, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&b->d_offsets, (size_t)(b->grid + 1) * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&b->d_status, sizeof(Status)) != cudaSuccess ||
       cudaMalloc(&b->d_out, NOBS * sizeof(double)) != cudaSuccess ||
       cudaMallocHost(&b->h_out, NOBS * sizeof(double)) != cudaSuccess) {
@@ -195,7 +334,7 @@ extern "C" int lb_batch_create(int capacity, int storage, void* cuda_stream, lb_
     return LB_ENOMEM;
   }
   if (cudaMemsetAsync(b->d_reps, 0, (size_t)capacity * rep_bytes(storage), b->stream) != cudaSuccess ||
-      cudaMemsetAsync(b->d_nitems, 0, sizeof(int), b->stream) != cudaSuccess ||
+      cudaMemsetAsync(b->d_offsets, 0, (size_t)(b->grid + 1) * sizeof(int), b->stream) != cudaSuccess ||
       cudaMemsetAsync(b->d_status, 0, sizeof(Status), b->stream) != cudaSuccess) {
     lb_batch_destroy(b);
     return LB_ECUDA;
@@ -215,7 +354,7 @@ extern "C" void lb_batch_destroy(lb_batch* b) {
   }
   cudaFree(b->d_reps);
   cudaFree(b->d_items);
-  cudaFree(b->d_nitems);
+  cudaFree(b->d_offsets);
   cudaFree(b->d_status);
   cudaFree(b->d_partials);
   cudaFree(b->d_out);
@@ -244,6 +383,8 @@ extern "C" int lb_batch_add(lb_batch* b, int nx, int ny, const lb_params* p, uin
   s.p = *p;
   s.g = g;
   fill_physd(*p, &s.ph);
+  const int phys = b->storage == LB_F64 ? phys_index<double>(b, s.ph) : phys_index<float>(b, s.ph);
+  if (phys < 0) return LB_EBUSY;  // more distinct physics sets than one launch carries
   const size_t bytes = lb_state_bytes(nx, ny, p->storage);
   if (cudaMalloc(&s.buf[0], bytes) != cudaSuccess || cudaMalloc(&s.buf[1], bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -261,10 +402,10 @@ extern "C" int lb_batch_add(lb_batch* b, int nx, int ny, const lb_params* p, uin
   const size_t rb = rep_bytes(b->storage);
   unsigned char rec[sizeof(ReplicaDev<double>)];
   if (b->storage == LB_F64) {
-    ReplicaDev<double> r = make_record<double>(s, steps);
+    ReplicaDev<double> r = make_record<double>(s, phys, steps);
     memcpy(rec, &r, sizeof(r));
   } else {
-    ReplicaDev<float> r = make_record<float>(s, steps);
+    ReplicaDev<float> r = make_record<float>(s, phys, steps);
     memcpy(rec, &r, sizeof(r));
   }
   if (cudaMemcpyAsync((char*)b->d_reps + (size_t)k * rb, rec, rb, cudaMemcpyHostToDevice,
@@ -306,8 +447,8 @@ extern "C" int lb_batch_set_steps(lb_batch* b, int slot, int64_t steps) {
 }
 
 static cudaError_t batch_launch(lb_batch* b, cudaStream_t st) {
-  return launch_step_rows_batch(b->storage, b->d_reps, b->d_items, b->d_nitems, b->grid,
-                                b->d_status, st);
+  return launch_step_rows_batch(b->storage, b->d_reps, b->d_items, b->d_offsets, b->grid,
+                                b->table, b->nphys, b->d_status, st);
 }
 
 static int ensure_batch_graph(lb_batch* b) {
@@ -489,15 +630,18 @@ extern "C" int lb_batch_get_state(lb_batch* b, int slot, double* f) {
   return cudaStreamSynchronize(b->stream) == cudaSuccess ? LB_OK : LB_ECUDA;
 }
 
-extern "C" int lb_batch_autotune(lb_batch* b, int steps_per_candidate, int* rows_per_item) {
+extern "C" int lb_batch_autotune(lb_batch* b, int steps_per_candidate, int* layout,
+                                 int* rows_per_item) {
   if (!b || steps_per_candidate < 1) return LB_EINVAL;
-  const int cands[] = {16, 32, 64, 128, 256};
+  // (layout, longest piece): contiguous or packed work lists, uncut or cut
+  const int cands[][2] = {{0, 1 << 30}, {0, 512}, {1, 1 << 30}, {1, 512}, {1, 128}};
   float best_ms = -1.0f;
-  int best = b->rows_per_item;
+  int best_l = b->layout, best_r = b->rows_per_item;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return LB_ECUDA;
-  for (int c : cands) {
-    b->rows_per_item = c;
+  for (const auto& c : cands) {
+    b->layout = c[0];
+    b->rows_per_item = c[1];
     b->dirty = true;
     int rc = rebuild_items(b);
     if (rc) break;
@@ -510,16 +654,19 @@ extern "C" int lb_batch_autotune(lb_batch* b, int steps_per_candidate, int* rows
     cudaEventElapsedTime(&ms, e0, e1);
     if (best_ms < 0.0f || ms < best_ms) {
       best_ms = ms;
-      best = c;
+      best_l = c[0];
+      best_r = c[1];
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  b->rows_per_item = best;
+  b->layout = best_l;
+  b->rows_per_item = best_r;
   b->dirty = true;
   int rc = rebuild_items(b);
   if (rc) return rc;
-  if (rows_per_item) *rows_per_item = best;
+  if (layout) *layout = best_l;
+  if (rows_per_item) *rows_per_item = best_r;
   return best_ms < 0.0f ? LB_ECUDA : LB_OK;
 }
 

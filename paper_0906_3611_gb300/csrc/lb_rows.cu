@@ -224,6 +224,7 @@ struct RowsLoop {
   int* s_abort;
   Status* status;
   int x0, ylo, nstage, ring;
+  C Uwall;
   // this thread (a compute thread serves column x = x0 + t)
   int warp, lane, t, x, plane;
   bool active;
@@ -236,11 +237,11 @@ struct RowsLoop {
   int bad;
 
   __device__ __forceinline__ RowsLoop(const T2* __restrict__ src_, T2* __restrict__ dst,
-                                      const Geom& g_, const Phys<C>& ph_, int x0_, int x1,
+                                      const Geom& g_, const Phys<C>& ph_, C Uwall_, int x0_, int x1,
                                       int ylo_, int yhi, const RowsSmem<STORAGE>& sm_, int ring_,
                                       int* s_abort_, Status* status_)
       : src(src_), g(g_), ph(ph_), sm(sm_), s_abort(s_abort_), status(status_), x0(x0_),
-        ylo(ylo_), nstage((yhi - ylo_) + 4), ring(ring_) {
+        ylo(ylo_), nstage((yhi - ylo_) + 4), ring(ring_), Uwall(Uwall_) {
     warp = threadIdx.x >> 5;
     lane = threadIdx.x & 31;
     t = (warp < NCW) ? (int)threadIdx.x : 0;
@@ -610,7 +611,7 @@ struct RowsLoop {
       for (int i = 1; i < 9; ++i) {
         const int yd = o + Q9::cy(i);
         if (yd < 0 || yd >= g.ny) {
-          const C Uw = (yd >= g.ny) ? ph.Uwall : -ph.Uwall;
+          const C Uw = (yd >= g.ny) ? Uwall : -Uwall;
           d[i] = pfma(pbc(-C(6) * wq<C>(i) * C(Q9::cx(i)) * Uw), rho, d[i]);
         }
       }
@@ -640,9 +641,10 @@ template <int STORAGE>
 __device__ __forceinline__ void rows_range(
     const typename PairStore<STORAGE>::T2* __restrict__ src,
     typename PairStore<STORAGE>::T2* __restrict__ dst, const Geom& g,
-    const Phys<typename Store<STORAGE>::C>& ph, int x0, int x1, int ylo, int yhi,
-    const RowsSmem<STORAGE>& sm, int& ring, int* s_abort, Status* status, int& bad) {
-  RowsLoop<STORAGE> L(src, dst, g, ph, x0, x1, ylo, yhi, sm, ring, s_abort, status);
+    const Phys<typename Store<STORAGE>::C>& ph, typename Store<STORAGE>::C Uwall, int x0, int x1,
+    int ylo, int yhi, const RowsSmem<STORAGE>& sm, int& ring, int* s_abort, Status* status,
+    int& bad) {
+  RowsLoop<STORAGE> L(src, dst, g, ph, Uwall, x0, x1, ylo, yhi, sm, ring, s_abort, status);
   if (L.warp == NCW)
     L.produce();
   else
@@ -673,28 +675,32 @@ __global__ void __launch_bounds__(RTHREADS, RowsCfg<STORAGE>::MINB)
   }
   __syncthreads();
   int ring = 0, bad = 0;
-  rows_range<STORAGE>(src, dst, g, ph, x0, x1, ylo, yhi, sm, ring, &s_abort, status, bad);
+  rows_range<STORAGE>(src, dst, g, ph, ph.Uwall, x0, x1, ylo, yhi, sm, ring, &s_abort, status, bad);
   if (bad) atomicAdd(&status->bad_rho, (unsigned)bad);
 }
 
-// Batched ensemble: a persistent grid walks a work list of (replica, strip,
-// row range) items; each replica keeps its own geometry, constants, buffer
-// parity and step budget in device memory.  The CTA that finishes the last
+// Batched ensemble: CTA c of a persistent grid walks items [offsets[c],
+// offsets[c+1]) of a work list of (replica, strip, row range) pieces; each
+// replica keeps its own geometry, constants, buffer parity and step budget in
+// device memory.  The CTA that finishes the last
 // item of a replica in a launch flips its parity and spends one step of its
 // budget; replicas with no budget left are skipped.
-template <int STORAGE>
+// ONE: every replica uses physics set 0 (the constants are then addressed
+// like the single-lattice kernel's parameters, without an index computation).
+template <int STORAGE, bool ONE>
 __global__ void __launch_bounds__(RTHREADS, RowsCfg<STORAGE>::MINB)
     k_rows_batch(ReplicaDev<typename Store<STORAGE>::C>* __restrict__ reps,
-                 const WorkItem* __restrict__ items, const int* __restrict__ n_items,
-                 Status* status) {
+                 const WorkItem* __restrict__ items, const int* __restrict__ offsets,
+                 Status* status, const __grid_constant__ PhysTable<typename Store<STORAGE>::C> tab) {
   using T2 = typename PairStore<STORAGE>::T2;
   using C = typename Store<STORAGE>::C;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_abort;
   __shared__ int s_skip;
+  __shared__ int s_phys;
+  __shared__ C s_U;
   __shared__ WorkItem s_item;
   __shared__ Geom s_g;
-  __shared__ Phys<C> s_ph;
   __shared__ const T2* s_src;
   __shared__ T2* s_dst;
   RowsSmem<STORAGE> sm(smem);
@@ -703,22 +709,23 @@ __global__ void __launch_bounds__(RTHREADS, RowsCfg<STORAGE>::MINB)
     s_abort = 0;
   }
   int ring = 0, bad = 0;
-  const int n = *n_items;
-  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+  const int it1 = offsets[blockIdx.x + 1];
+  for (int it = offsets[blockIdx.x]; it < it1; ++it) {
     __syncthreads();  // the previous item is finished by every thread
     if (threadIdx.x == 0) {
       s_item = items[it];
       const ReplicaDev<C>& R = reps[s_item.replica];
       s_skip = R.remaining <= 0;
       s_g = R.g;
-      s_ph = R.ph;
+      s_phys = R.phys;
+      s_U = R.Uwall;
       s_src = (const T2*)R.buf[R.parity];
       s_dst = (T2*)R.buf[1 - R.parity];
     }
     __syncthreads();
     if (s_skip) continue;
-    rows_range<STORAGE>(s_src, s_dst, s_g, s_ph, s_item.x0, s_item.x1, s_item.ylo, s_item.yhi, sm,
-                        ring, &s_abort, status, bad);
+    rows_range<STORAGE>(s_src, s_dst, s_g, tab.p[ONE ? 0 : s_phys], s_U, s_item.x0, s_item.x1,
+                        s_item.ylo, s_item.yhi, sm, ring, &s_abort, status, bad);
     __syncthreads();
     if (s_abort) break;
     if (threadIdx.x == 0) {
@@ -744,9 +751,16 @@ static int resident_blocks() {
     const size_t smem = rows_smem_bytes<STORAGE>();
     int per_sm = 0, dev = 0, sms = 0;
     if (BATCH) {
-      cudaFuncSetAttribute(k_rows_batch<STORAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(k_rows_batch<STORAGE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows_batch<STORAGE>, RTHREADS, smem);
+      cudaFuncSetAttribute(k_rows_batch<STORAGE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+      int per_sm1 = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows_batch<STORAGE, false>, RTHREADS,
+                                                    smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, k_rows_batch<STORAGE, true>, RTHREADS,
+                                                    smem);
+      if (per_sm1 < per_sm) per_sm = per_sm1;
     } else {
       cudaFuncSetAttribute(k_rows<STORAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows<STORAGE>, RTHREADS, smem);
@@ -818,21 +832,26 @@ cudaError_t launch_step_rows(int storage, const void* src, void* dst, const Geom
 }
 
 template <int STORAGE>
-static cudaError_t rows_batch_t(void* reps, const WorkItem* items, const int* n_items, int grid,
-                                Status* status, cudaStream_t st) {
+static cudaError_t rows_batch_t(void* reps, const WorkItem* items, const int* offsets, int grid,
+                                const void* table, int nphys, Status* status, cudaStream_t st) {
   using C = typename Store<STORAGE>::C;
-  k_rows_batch<STORAGE><<<grid, RTHREADS, rows_smem_bytes<STORAGE>(), st>>>(
-      (ReplicaDev<C>*)reps, items, n_items, status);
+  if (nphys <= 1)
+    k_rows_batch<STORAGE, true><<<grid, RTHREADS, rows_smem_bytes<STORAGE>(), st>>>(
+        (ReplicaDev<C>*)reps, items, offsets, status, *(const PhysTable<C>*)table);
+  else
+    k_rows_batch<STORAGE, false><<<grid, RTHREADS, rows_smem_bytes<STORAGE>(), st>>>(
+        (ReplicaDev<C>*)reps, items, offsets, status, *(const PhysTable<C>*)table);
   return cudaGetLastError();
 }
 
 cudaError_t launch_step_rows_batch(int storage, void* reps, const WorkItem* items,
-                                   const int* n_items, int grid, Status* status, cudaStream_t st) {
+                                   const int* offsets, int grid, const void* table, int nphys,
+                                   Status* status, cudaStream_t st) {
   switch (storage) {
-    case LB_F64: return rows_batch_t<LB_F64>(reps, items, n_items, grid, status, st);
-    case LB_F32: return rows_batch_t<LB_F32>(reps, items, n_items, grid, status, st);
-    case LB_BF16_DEV: return rows_batch_t<LB_BF16_DEV>(reps, items, n_items, grid, status, st);
-    case LB_F16_DEV: return rows_batch_t<LB_F16_DEV>(reps, items, n_items, grid, status, st);
+    case LB_F64: return rows_batch_t<LB_F64>(reps, items, offsets, grid, table, nphys, status, st);
+    case LB_F32: return rows_batch_t<LB_F32>(reps, items, offsets, grid, table, nphys, status, st);
+    case LB_BF16_DEV: return rows_batch_t<LB_BF16_DEV>(reps, items, offsets, grid, table, nphys, status, st);
+    case LB_F16_DEV: return rows_batch_t<LB_F16_DEV>(reps, items, offsets, grid, table, nphys, status, st);
   }
   return cudaErrorInvalidValue;
 }

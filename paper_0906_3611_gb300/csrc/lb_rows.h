@@ -5,11 +5,21 @@
 
 namespace lbk {
 
+// Distinct physics sets of a batched ensemble, passed by value as a kernel
+// parameter (constant bank: the kernel re-reads the constants at no register
+// cost).  The wall speed is per replica and is not part of a set.
+constexpr int kMaxPhysSets = 16;
+template <typename C>
+struct PhysTable {
+  Phys<C> p[kMaxPhysSets];
+};
+
 // Per-replica record of a batched ensemble, in device memory.
 template <typename C>
 struct ReplicaDev {
   Geom g;
-  Phys<C> ph;
+  int phys;            // index into the launch's PhysTable
+  C Uwall;             // Couette wall speed of this replica
   void* buf[2];        // the two population buffers
   int nitems;          // work items of this replica per step
   int parity;          // buffer holding the current state
@@ -46,7 +56,12 @@ cudaError_t launch_step_rows(int storage, const void* src, void* dst, const Geom
 
 // One step of every replica with budget left; `reps` is a device array of
 // ReplicaDev<float> (FP32 and 16-bit storages) or ReplicaDev<double> (FP64).
+// CTA c of the persistent grid works on items [offsets[c], offsets[c+1]);
+// `table` is a host PhysTable<float> (FP32 and 16-bit storages) or
+// PhysTable<double> (FP64) with `nphys` sets in use, copied into the launch's
+// parameters.
 cudaError_t launch_step_rows_batch(int storage, void* reps, const WorkItem* items,
-                                   const int* n_items, int grid, Status* status, cudaStream_t st);
+                                   const int* offsets, int grid, const void* table, int nphys,
+                                   Status* status, cudaStream_t st);
 
 }  // namespace lbk

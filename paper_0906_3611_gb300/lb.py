@@ -81,7 +81,8 @@ def _load():
         "lb_batch_poll": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
         "lb_batch_observables": (ctypes.c_int, [vp, ctypes.c_int, dp, dp, dp, dp]),
         "lb_batch_get_state": (ctypes.c_int, [vp, ctypes.c_int, dp]),
-        "lb_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+        "lb_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                             ctypes.POINTER(ctypes.c_int)]),
         "lb_batch_status": (ctypes.c_int, [vp]),
         "lb_batch_destroy": (None, [vp]),
     }
@@ -245,10 +246,12 @@ def lb_batch_get_state(b: int, slot: int, f: np.ndarray) -> None:
     _check(_lib.lb_batch_get_state(b, slot, _dp(f)), "lb_batch_get_state")
 
 
-def lb_batch_autotune(b: int, steps_per_candidate: int) -> int:
+def lb_batch_autotune(b: int, steps_per_candidate: int) -> tuple[int, int]:
+    layout = ctypes.c_int(0)
     rows = ctypes.c_int(0)
-    _check(_lib.lb_batch_autotune(b, steps_per_candidate, ctypes.byref(rows)), "lb_batch_autotune")
-    return rows.value
+    _check(_lib.lb_batch_autotune(b, steps_per_candidate, ctypes.byref(layout), ctypes.byref(rows)),
+           "lb_batch_autotune")
+    return layout.value, rows.value
 
 
 def lb_batch_status(b: int) -> int:
@@ -392,7 +395,8 @@ class Batch:
         lb_batch_get_state(self.h, slot, f)
         return f
 
-    def autotune(self, steps_per_candidate: int = 4) -> int:
+    def autotune(self, steps_per_candidate: int = 4) -> tuple[int, int]:
+        """(layout, longest piece in rows) chosen by the library's autotuner."""
         return lb_batch_autotune(self.h, steps_per_candidate)
 
     def status(self) -> int:

@@ -108,8 +108,8 @@ def test_slots_are_reused_after_remove(lb, monkeypatch):
 def test_autotune_keeps_results_exact(lb, monkeypatch):
     b = lb.Batch(4, lb.LB_F32)
     k = b.add(512, 256, _p(lb, CFG, lb.LB_F32, 1, 0.02), 7, 1000)
-    rows = b.autotune(2)  # 5 candidates x (2 + 1) steps
-    assert rows in (16, 32, 64, 128, 256)
+    layout, rows = b.autotune(2)  # 5 candidates x (2 + 1) steps
+    assert (layout, rows) in ((0, 1 << 30), (0, 512), (1, 1 << 30), (1, 512), (1, 128))
     b.run(5)
     rem, done = b.poll()
     n = int(done[k])
