@@ -122,7 +122,7 @@ static int create_common(int nx, int ny, const lb_params* p, void* stream, void*
   }
   // step kernel: the row-streaming kernel where it applies, else the tile
   // kernel; LB_STEP_KERNEL=tile|rows forces one (for testing both paths)
-  // (by default the row kernel serves lattices at least one strip wide)
+  // (by default the row kernel serves lattices at least 128 columns wide)
   const char* kern = getenv("LB_STEP_KERNEL");
   const bool rows_ok = rows_supported(h->g, p->storage);
   if (kern && strcmp(kern, "tile") == 0)
@@ -134,7 +134,7 @@ static int create_common(int nx, int ny, const lb_params* p, void* stream, void*
     }
     h->use_rows = 1;
   } else
-    h->use_rows = (rows_ok && nx >= rows_strip_width()) ? 1 : 0;
+    h->use_rows = (rows_ok && nx >= 128) ? 1 : 0;
   *out = h;
   return LB_OK;
 }

@@ -166,14 +166,15 @@ static void build_packed(lb_batch* b, std::vector<WorkItem>& items, std::vector<
     for (int k = 0; k < b->capacity; ++k) {
       const Slot& s = b->slots[k];
       if (!s.used) continue;
-      const int nstrips = rows_nstrips(s.nx);
+      const int width = rows_strip_width(b->storage);
+    const int nstrips = rows_nstrips(s.nx, width);
       long long kr = (s.ny + hmax - 1) / hmax;
       if (kr > s.ny) kr = s.ny;
       for (long long q = 0; q < kr; ++q) {
         const int ylo = (int)(q * s.ny / kr), yhi = (int)((q + 1) * s.ny / kr);
         for (int j = 0; j < nstrips; ++j) {
-          pieces.push_back(Piece{yhi - ylo + 4, WorkItem{k, rows_strip_x0(j, nstrips, s.nx),
-                                                         rows_strip_x0(j + 1, nstrips, s.nx),
+          pieces.push_back(Piece{yhi - ylo + 4, WorkItem{k, rows_strip_x0(j, nstrips, s.nx, width),
+                                                         rows_strip_x0(j + 1, nstrips, s.nx, width),
                                                          ylo, yhi}});
           ++counts[k];
         }
@@ -235,16 +236,17 @@ static void build_contiguous(lb_batch* b, std::vector<WorkItem>& items, std::vec
                              std::vector<int>& counts) {
   long long total = 0;
   for (int k = 0; k < b->capacity; ++k)
-    if (b->slots[k].used) total += (long long)rows_nstrips(b->slots[k].nx) * b->slots[k].ny;
+    if (b->slots[k].used) total += (long long)rows_nstrips(b->slots[k].nx, rows_strip_width(b->storage)) * b->slots[k].ny;
   const long long per = total > 0 ? (total + b->grid - 1) / b->grid : 1;
   int cta = 0;
   long long left = per;
   for (int k = 0; k < b->capacity; ++k) {
     const Slot& s = b->slots[k];
     if (!s.used) continue;
-    const int nstrips = rows_nstrips(s.nx);
+    const int width = rows_strip_width(b->storage);
+    const int nstrips = rows_nstrips(s.nx, width);
     for (int j = 0; j < nstrips; ++j) {
-      const int x0 = rows_strip_x0(j, nstrips, s.nx), x1 = rows_strip_x0(j + 1, nstrips, s.nx);
+      const int x0 = rows_strip_x0(j, nstrips, s.nx, width), x1 = rows_strip_x0(j + 1, nstrips, s.nx, width);
       int y = 0;
       while (y < s.ny) {
         long long take = std::min<long long>(std::min<long long>(s.ny - y, left), b->rows_per_item);

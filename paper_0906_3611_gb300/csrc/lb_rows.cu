@@ -1,9 +1,9 @@
 // lb_rows.cu -- row-streaming fused step kernel (the bandwidth path).
 //
-// Each CTA owns a strip of RX = 128 columns [x0, x1) and a contiguous range
-// of rows, and walks down the rows once.  Row r of the state f(t) (the 9
-// direction planes, both species of each site side by side, columns
-// x0-SOFF .. x0+RX+SOFF-1, periodic in x) is staged in shared memory by bulk
+// Each CTA owns a strip of 32 NCW columns [x0, x1) (128 for every storage)
+// and a contiguous range of rows, and walks down the rows once.  Row r of the
+// state f(t) (the 9 direction planes, both species of each site side by side,
+// columns x0-SOFF .. x1+SOFF-1, periodic in x) is staged in shared memory by bulk
 // asynchronous copies (the TMA engine, cp.async.bulk) into a ring of NSLOT
 // slots.  A "full" mbarrier per slot counts the copied bytes; an "empty"
 // mbarrier per slot counts the compute warps that are done with it.
@@ -38,11 +38,9 @@
 
 namespace lbk {
 
-constexpr int RX = 128;            // strip columns (a multiple of 32)
-constexpr int NCW = RX / 32;       // compute warps
-constexpr int RTHREADS = RX + 32;  // compute warps + 1 staging warp
-constexpr int WEXT = 32 + 4;       // a compute warp's row buffer: 32 columns + 2 + 2 halo
+constexpr int WEXT = 32 + 4;  // a compute warp's row buffer: 32 columns + 2 + 2 halo
 
+// NCW: compute warps (the strip is 32 NCW columns wide; one more warp stages);
 // SOFF: halo sites staged on each side (>= 2, a 16-byte multiple of pairs);
 // NSLOT: ring depth (a power of two makes the slot arithmetic cheap where the
 // shared memory allows it); MINB: CTAs per SM the register budget is sized for;
@@ -54,28 +52,36 @@ template <int STORAGE>
 struct RowsCfg;
 template <>
 struct RowsCfg<LB_F64> {
-  static constexpr int SOFF = 2, NSLOT = 5, MINB = 2;  // 16-byte pairs
+  static constexpr int NCW = 4, SOFF = 2, NSLOT = 5, MINB = 2;  // 16-byte pairs
   static constexpr bool PIPE = true, LAG = true;
 };
 template <>
 struct RowsCfg<LB_F32> {
-  static constexpr int SOFF = 2, NSLOT = 7, MINB = 3;  // 8-byte pairs
+  static constexpr int NCW = 4, SOFF = 2, NSLOT = 7, MINB = 3;  // 8-byte pairs
   static constexpr bool PIPE = true, LAG = true;
 };
 template <>
 struct RowsCfg<LB_BF16_DEV> {
-  static constexpr int SOFF = 4, NSLOT = 8, MINB = 3;  // 4-byte pairs
+  static constexpr int NCW = 4, SOFF = 4, NSLOT = 8, MINB = 3;  // 4-byte pairs
   static constexpr bool PIPE = false, LAG = true;
 };
 template <>
 struct RowsCfg<LB_F16_DEV> {
-  static constexpr int SOFF = 4, NSLOT = 8, MINB = 3;
+  static constexpr int NCW = 4, SOFF = 4, NSLOT = 8, MINB = 3;
   static constexpr bool PIPE = false, LAG = true;
 };
 
 template <int STORAGE>
+constexpr int strip_cols() {
+  return 32 * RowsCfg<STORAGE>::NCW;
+}
+template <int STORAGE>
+constexpr int cta_threads() {
+  return 32 * (RowsCfg<STORAGE>::NCW + 1);
+}
+template <int STORAGE>
 constexpr int stage_width() {
-  return RX + 2 * RowsCfg<STORAGE>::SOFF;
+  return strip_cols<STORAGE>() + 2 * RowsCfg<STORAGE>::SOFF;
 }
 
 template <int STORAGE>
@@ -83,7 +89,7 @@ constexpr size_t rows_smem_bytes() {
   using T2 = typename PairStore<STORAGE>::T2;
   using P = typename PairOf<typename Store<STORAGE>::C>::P;
   return (size_t)RowsCfg<STORAGE>::NSLOT * 9 * stage_width<STORAGE>() * sizeof(T2) +
-         (size_t)NCW * 2 * WEXT * sizeof(P) + 2 * 8 * RowsCfg<STORAGE>::NSLOT;
+         (size_t)RowsCfg<STORAGE>::NCW * 2 * WEXT * sizeof(P) + 2 * 8 * RowsCfg<STORAGE>::NSLOT;
 }
 
 // ---- mbarrier / bulk-copy primitives (PTX) ----
@@ -146,7 +152,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, u
       : "memory");
 }
 
-// Stage row r (9 planes of site pairs, columns x0-SOFF .. x0+RX+SOFF-1
+// Stage row r (9 planes of site pairs, columns x0-SOFF .. x0+width+SOFF-1
 // wrapped in x) into `slot`.  Called by a whole warp: lane 0 posts the byte
 // count of the row on the slot's mbarrier, then lanes 0..8 each copy one plane
 // as one bulk copy per contiguous run of the periodic window (one run, or two
@@ -180,6 +186,7 @@ struct RowsSmem {
   using T2 = typename PairStore<STORAGE>::T2;
   using P = typename PairOf<typename Store<STORAGE>::C>::P;
   static constexpr int NSLOT = RowsCfg<STORAGE>::NSLOT;
+  static constexpr int NCW = RowsCfg<STORAGE>::NCW;
   static constexpr int SLOT = 9 * stage_width<STORAGE>();
   T2* stage;      // NSLOT slots of SLOT pairs
   P* rowbuf;      // per compute warp: WEXT rho pairs, WEXT psi pairs
@@ -216,6 +223,7 @@ struct RowsLoop {
   using P = typename PairOf<C>::P;
   static constexpr int SOFF = RowsCfg<STORAGE>::SOFF;
   static constexpr int NSLOT = RowsCfg<STORAGE>::NSLOT;
+  static constexpr int NCW = RowsCfg<STORAGE>::NCW;
   static constexpr int SW = stage_width<STORAGE>();
   static constexpr int SLOT = 9 * SW;
 
@@ -660,7 +668,7 @@ __device__ __forceinline__ void rows_range(
     int ylo, int yhi, const RowsSmem<STORAGE>& sm, int& ring, int* s_abort, Status* status,
     int& bad) {
   RowsLoop<STORAGE> L(src, dst, g, ph, Uwall, x0, x1, ylo, yhi, sm, ring, s_abort, status);
-  if (L.warp == NCW)
+  if (L.warp == RowsCfg<STORAGE>::NCW)
     L.produce();
   else
     L.consume();
@@ -670,7 +678,7 @@ __device__ __forceinline__ void rows_range(
 
 // Single lattice: CTA b owns strip b % nstrips and row range b / nstrips.
 template <int STORAGE>
-__global__ void __launch_bounds__(RTHREADS, RowsCfg<STORAGE>::MINB)
+__global__ void __launch_bounds__(cta_threads<STORAGE>(), RowsCfg<STORAGE>::MINB)
     k_rows(const typename PairStore<STORAGE>::T2* __restrict__ src,
            typename PairStore<STORAGE>::T2* __restrict__ dst, Geom g,
            Phys<typename Store<STORAGE>::C> ph, int nstrips, int kranges, Status* status) {
@@ -679,8 +687,8 @@ __global__ void __launch_bounds__(RTHREADS, RowsCfg<STORAGE>::MINB)
   RowsSmem<STORAGE> sm(smem);
   const int strip = blockIdx.x % nstrips;
   const int range = blockIdx.x / nstrips;
-  const int x0 = rows_strip_x0(strip, nstrips, g.nx);
-  const int x1 = rows_strip_x0(strip + 1, nstrips, g.nx);
+  const int x0 = rows_strip_x0(strip, nstrips, g.nx, strip_cols<STORAGE>());
+  const int x1 = rows_strip_x0(strip + 1, nstrips, g.nx, strip_cols<STORAGE>());
   const int ylo = (int)((long long)range * g.ny / kranges);
   const int yhi = (int)((long long)(range + 1) * g.ny / kranges);
   if (yhi <= ylo) return;
@@ -703,7 +711,7 @@ __global__ void __launch_bounds__(RTHREADS, RowsCfg<STORAGE>::MINB)
 // ONE: every replica uses physics set 0 (the constants are then addressed
 // like the single-lattice kernel's parameters, without an index computation).
 template <int STORAGE, bool ONE>
-__global__ void __launch_bounds__(RTHREADS, RowsCfg<STORAGE>::MINB)
+__global__ void __launch_bounds__(cta_threads<STORAGE>(), RowsCfg<STORAGE>::MINB)
     k_rows_batch(ReplicaDev<typename Store<STORAGE>::C>* __restrict__ reps,
                  const WorkItem* __restrict__ items, const int* __restrict__ offsets,
                  Status* status, const __grid_constant__ PhysTable<typename Store<STORAGE>::C> tab) {
@@ -771,14 +779,15 @@ static int resident_blocks() {
       cudaFuncSetAttribute(k_rows_batch<STORAGE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
       int per_sm1 = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows_batch<STORAGE, false>, RTHREADS,
-                                                    smem);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, k_rows_batch<STORAGE, true>, RTHREADS,
-                                                    smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows_batch<STORAGE, false>,
+                                                    cta_threads<STORAGE>(), smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, k_rows_batch<STORAGE, true>,
+                                                    cta_threads<STORAGE>(), smem);
       if (per_sm1 < per_sm) per_sm = per_sm1;
     } else {
       cudaFuncSetAttribute(k_rows<STORAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows<STORAGE>, RTHREADS, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows<STORAGE>, cta_threads<STORAGE>(),
+                                                    smem);
     }
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -799,9 +808,14 @@ static int resident(int storage, bool batch) {
   return 0;
 }
 
-int rows_strip_width() {
-  static_assert(RX == 128, "rows_strip_x0 assumes 128-column strips");
-  return RX;
+int rows_strip_width(int storage) {
+  switch (storage) {
+    case LB_F64: return strip_cols<LB_F64>();
+    case LB_F32: return strip_cols<LB_F32>();
+    case LB_BF16_DEV: return strip_cols<LB_BF16_DEV>();
+    case LB_F16_DEV: return strip_cols<LB_F16_DEV>();
+  }
+  return 0;
 }
 
 bool rows_geometry_ok(const Geom& g, int storage) {
@@ -825,12 +839,12 @@ template <int STORAGE>
 static cudaError_t rows_t(const void* src, void* dst, const Geom& g, const PhysD& pd,
                           Status* status, cudaStream_t st) {
   using T2 = typename PairStore<STORAGE>::T2;
-  const int nstrips = rows_nstrips(g.nx);
+  const int nstrips = rows_nstrips(g.nx, strip_cols<STORAGE>());
   int k = resident(STORAGE, false) / nstrips;
   if (k < 1) k = 1;
   if (k > g.ny) k = g.ny;
   const size_t smem = rows_smem_bytes<STORAGE>();
-  k_rows<STORAGE><<<nstrips * k, RTHREADS, smem, st>>>(
+  k_rows<STORAGE><<<nstrips * k, cta_threads<STORAGE>(), smem, st>>>(
       (const T2*)src, (T2*)dst, g, make_phys<typename Store<STORAGE>::C>(pd), nstrips, k, status);
   return cudaGetLastError();
 }
@@ -851,10 +865,10 @@ static cudaError_t rows_batch_t(void* reps, const WorkItem* items, const int* of
                                 const void* table, int nphys, Status* status, cudaStream_t st) {
   using C = typename Store<STORAGE>::C;
   if (nphys <= 1)
-    k_rows_batch<STORAGE, true><<<grid, RTHREADS, rows_smem_bytes<STORAGE>(), st>>>(
+    k_rows_batch<STORAGE, true><<<grid, cta_threads<STORAGE>(), rows_smem_bytes<STORAGE>(), st>>>(
         (ReplicaDev<C>*)reps, items, offsets, status, *(const PhysTable<C>*)table);
   else
-    k_rows_batch<STORAGE, false><<<grid, RTHREADS, rows_smem_bytes<STORAGE>(), st>>>(
+    k_rows_batch<STORAGE, false><<<grid, cta_threads<STORAGE>(), rows_smem_bytes<STORAGE>(), st>>>(
         (ReplicaDev<C>*)reps, items, offsets, status, *(const PhysTable<C>*)table);
   return cudaGetLastError();
 }

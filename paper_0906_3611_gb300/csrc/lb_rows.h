@@ -33,13 +33,14 @@ struct WorkItem {
   int replica, x0, x1, ylo, yhi;
 };
 
-// Columns per strip of the row-streaming kernels.
-int rows_strip_width();
+// Columns per strip of the row-streaming kernels for a storage (32 per
+// compute warp of a CTA).
+int rows_strip_width(int storage);
 
-// Strips of a lattice row: 128 columns (the last one ragged).
-__host__ __device__ inline int rows_nstrips(int nx) { return (nx + 127) / 128; }
-__host__ __device__ inline int rows_strip_x0(int j, int nstrips, int nx) {
-  return j >= nstrips ? nx : j * 128;
+// Strips of a lattice row: `width` columns (the last one ragged).
+__host__ __device__ inline int rows_nstrips(int nx, int width) { return (nx + width - 1) / width; }
+__host__ __device__ inline int rows_strip_x0(int j, int nstrips, int nx, int width) {
+  return j >= nstrips ? nx : j * width;
 }
 
 // True if the row-streaming kernel handles this lattice shape and storage.
