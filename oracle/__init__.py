@@ -70,6 +70,8 @@ def _load():
         lib.lbo_init_densities.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                                            ctypes.c_int, dp, dp]
         lib.lbo_init_densities.restype = None
+        lib.lbo_shear_diagnostics.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, dp]
+        lib.lbo_shear_diagnostics.restype = ctypes.c_long
         lib.lbo_max_threads.argtypes = []
         lib.lbo_max_threads.restype = ctypes.c_int
         _lib = lib
@@ -84,14 +86,17 @@ def _dp(a: np.ndarray):
 def params_vector(p: dict) -> np.ndarray:
     """Pack a parameter dict into the oracle's parameter vector.
 
-    Keys: tau (pair), rho0, G_AB, Ga (pair), Gr (pair), boundary, U_wall.
+    Keys: tau (pair), rho0, G_AB, Ga (pair), Gr (pair), boundary, U_wall,
+    g_kolmo (Kolmogorov body acceleration amplitude, default 0) and k_kolmo
+    (its wave number, default 1).
     """
     tau = p.get("tau", (1.0, 1.0))
     Ga = p.get("Ga", (0.0, 0.0))
     Gr = p.get("Gr", (0.0, 0.0))
     return np.array([tau[0], tau[1], p.get("rho0", 1.0), p.get("G_AB", 0.0),
                      Ga[0], Ga[1], Gr[0], Gr[1], float(p.get("boundary", PERIODIC)),
-                     p.get("U_wall", 0.0)], dtype=np.float64)
+                     p.get("U_wall", 0.0), p.get("g_kolmo", 0.0), float(p.get("k_kolmo", 1))],
+                    dtype=np.float64)
 
 
 def tables():
@@ -148,6 +153,17 @@ def observables(f: np.ndarray, p: dict) -> dict:
     if bad < 0:
         raise MemoryError("oracle observables: allocation failed")
     return {"rho": rho, "u": u, "stress": stress, "mass": mass, "bad": int(bad)}
+
+
+def shear_diagnostics(f: np.ndarray, p: dict) -> dict:
+    """Sec. VII diagnostics of a state: U_k (sine amplitude of the line-averaged
+    x velocity at the forcing wave number; R = U_k / U0) and I_AB (Eq. (INDICATOR))."""
+    lib = _load()
+    _, _, ny, nx = f.shape
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.zeros(2)
+    bad = lib.lbo_shear_diagnostics(_dp(f), nx, ny, _dp(params_vector(p)), _dp(out))
+    return {"U_k": float(out[0]), "I_AB": float(out[1]), "bad": int(bad)}
 
 
 def philox4x32_10(ctr, key):

@@ -39,10 +39,17 @@
  * Parameter vector prm[] (doubles):
  *   0 tau_A   1 tau_B   2 rho0   3 G_AB   4 Ga_A  5 Ga_B  6 Gr_A  7 Gr_B
  *   8 boundary (0 periodic, 1 Couette)    9 U_wall
+ *   10 g (Kolmogorov body acceleration amplitude)   11 k (its wave number)
+ *
+ * Kolmogorov shear (Sec. VII: a flow U_x = U0 sin(ky) imposed by a volumetric
+ * body force): every species feels the force density rho_s g sin(2 pi k y / ny)
+ * along x, added to F_s of Eq. (FORCE) so that it enters the shifted velocity
+ * of Eq. (be) like the interaction forces.
  *
  * Build with -ffp-contract=off so that results do not depend on whether the
  * host compiler fuses multiply-adds.
  */
+#define _GNU_SOURCE 1
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -161,6 +168,7 @@ void lbo_forces(const double *rho, int nx, int ny, const double *prm, double *F)
     for (int s = 0; s < 2; ++s) {
       const int so = 1 - s;
       const double Ga = prm[4 + s], Gr = prm[6 + s];
+      const double body = prm[10] * sin(2.0 * M_PI * prm[11] * (double)y / (double)ny);
       for (int x = 0; x < nx; ++x) {
         double sa_x = 0, sa_y = 0, sr_x = 0, sr_y = 0, sx_x = 0, sx_y = 0;
         for (int j = 1; j < 25; ++j) {
@@ -181,7 +189,8 @@ void lbo_forces(const double *rho, int nx, int ny, const double *prm, double *F)
         const double Fr_x = -Gr * pc * sr_x, Fr_y = -Gr * pc * sr_y;
         const double Fx_x = -(GAB / (rho0 * rho0)) * rc * sx_x;
         const double Fx_y = -(GAB / (rho0 * rho0)) * rc * sx_y;
-        F[(((size_t)s * 2 + 0) * ny + y) * nx + x] = Fa_x + Fr_x + Fx_x;
+        const double Fb_x = rc * body;  /* Kolmogorov body force */
+        F[(((size_t)s * 2 + 0) * ny + y) * nx + x] = Fa_x + Fr_x + Fx_x + Fb_x;
         F[(((size_t)s * 2 + 1) * ny + y) * nx + x] = Fa_y + Fr_y + Fx_y;
       }
     }
@@ -386,6 +395,48 @@ long lbo_observables(const double *f, int nx, int ny, const double *prm,
     stress[2] = couette ? wb / nx : 0.0;
   }
   free(rho); free(F); free(v);
+  return bad;
+}
+
+/* ---- Shear diagnostics (Sec. VII).
+ *   out[0] = U_k: the sine amplitude at the forcing wave number k of the
+ *            line-averaged x velocity Ubar(y) = sum_x u_x(x, y) / nx, i.e.
+ *            (2/ny) sum_y Ubar(y) sin(2 pi k y / ny); the response of Eq.
+ *            (RESPONSE) is R = U_k / U0.  u is the paper's common velocity.
+ *   out[1] = I_AB of Eq. (INDICATOR): -sum_{x,y} grad rho_A . grad rho_B, with
+ *            central differences (rho(r + e) - rho(r - e)) / 2, periodic in x,
+ *            and in y periodic or mirrored about the walls as the force stencil.
+ * Returns the number of (site, species) pairs with rho_s <= 0. ---- */
+long lbo_shear_diagnostics(const double *f, int nx, int ny, const double *prm, double *out) {
+  const size_t N = (size_t)nx * ny;
+  const int couette = (int)prm[8];
+  double *rho = (double *)malloc(2 * N * sizeof(double));
+  double *u = (double *)malloc(2 * N * sizeof(double));
+  if (!rho || !u) {
+    free(rho); free(u);
+    return -1;
+  }
+  const long bad = lbo_observables(f, nx, ny, prm, rho, u, NULL, NULL);
+  double uk = 0.0, iab = 0.0;
+  for (int y = 0; y < ny; ++y) {
+    double ubar = 0.0;
+    for (int x = 0; x < nx; ++x) ubar += u[(size_t)y * nx + x];
+    uk += (ubar / nx) * sin(2.0 * M_PI * prm[11] * (double)y / (double)ny);
+    const int ym = stencil_row(y - 1, ny, couette), yp = stencil_row(y + 1, ny, couette);
+    for (int x = 0; x < nx; ++x) {
+      const int xm = wrap(x - 1, nx), xp = wrap(x + 1, nx);
+      double g[2][2];
+      for (int s = 0; s < 2; ++s) {
+        const double *r = rho + (size_t)s * N;
+        g[s][0] = 0.5 * (r[(size_t)y * nx + xp] - r[(size_t)y * nx + xm]);
+        g[s][1] = 0.5 * (r[(size_t)yp * nx + x] - r[(size_t)ym * nx + x]);
+      }
+      iab -= g[0][0] * g[1][0] + g[0][1] * g[1][1];
+    }
+  }
+  out[0] = 2.0 * uk / ny;
+  out[1] = iab;
+  free(rho); free(u);
   return bad;
 }
 
