@@ -105,6 +105,10 @@ typedef struct {
                         taken in FP64                                        */
   int init_kind;     /* LB_INIT_UNIFORM_NOISE or LB_INIT_BERNOULLI              */
   double init[6];    /* recipe parameters, see the LB_INIT_* kinds             */
+  double g_kolmo;    /* Kolmogorov shear (Sec. VII): every species feels the
+                        force density rho_s g_kolmo sin(2 pi k_kolmo y / ny)
+                        along x, added to F_s of Eq. (FORCE); 0 = off        */
+  int k_kolmo;       /* its wave number (>= 1 when g_kolmo != 0)               */
 } lb_params;
 
 /* Bytes of one population buffer: 9 direction planes of ny rows of pitch
@@ -151,6 +155,17 @@ LB_API int lb_step(lb_handle *h, int64_t n);
  *                 wall length; 0 for LB_PERIODIC);
  *   mass[4]       { sum rho_A, sum rho_B, P_x, P_y }, P = sum_s sum_i f_is c_i. */
 LB_API int lb_observables(lb_handle *h, double *rho, double *u, double *stress, double *mass);
+
+/* Shear diagnostics of the current state (Sec. VII); synchronises.
+ *   *u_k  the sine amplitude at the wave number k_kolmo of the line-averaged
+ *         x velocity Ubar(y) = sum_x u_x(x, y) / nx, i.e. (2/ny) sum_y Ubar(y)
+ *         sin(2 pi k y / ny), u the common velocity; the response of
+ *         Eq. (RESPONSE) is R = u_k / U0;
+ *   *i_ab Eq. (INDICATOR): -sum_{x,y} grad rho_A . grad rho_B, central
+ *         differences, periodic in x, in y periodic or mirrored about the
+ *         walls like the force stencil.
+ * Either pointer may be NULL. */
+LB_API int lb_shear_diagnostics(lb_handle *h, double *u_k, double *i_ab);
 
 /* Copy the state out as FP64 (layout above); synchronises. */
 LB_API int lb_get_state(lb_handle *h, double *f);

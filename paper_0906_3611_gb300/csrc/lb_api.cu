@@ -56,8 +56,9 @@ static int validate(int nx, int ny, const lb_params* p) {
   if (p->boundary != LB_PERIODIC && p->boundary != LB_COUETTE) return LB_EINVAL;
   if (elem_size(p->storage) == 0) return LB_EINVAL;
   if (p->init_kind != LB_INIT_UNIFORM_NOISE && p->init_kind != LB_INIT_BERNOULLI) return LB_EINVAL;
+  if (p->g_kolmo != 0.0 && p->k_kolmo < 1) return LB_EINVAL;
   const double vals[] = {p->G_AB, p->Ga[0], p->Ga[1], p->Gr[0], p->Gr[1], p->U_wall,
-                         p->rho_ref[0], p->rho_ref[1], p->tau[0], p->tau[1]};
+                         p->rho_ref[0], p->rho_ref[1], p->tau[0], p->tau[1], p->g_kolmo};
   for (double v : vals)
     if (!isfinite(v)) return LB_EINVAL;
   return LB_OK;
@@ -65,8 +66,7 @@ static int validate(int nx, int ny, const lb_params* p) {
 
 static void fill_phys(lb_handle* h) {
   const lb_params& p = h->p;
-  h->ph = physd_from_params(p.storage, p.tau, p.rho0, p.G_AB, p.Ga, p.Gr, p.boundary, p.U_wall,
-                            p.rho_ref);
+  h->ph = physd_from_params(p);
 }
 
 static int create_common(int nx, int ny, const lb_params* p, void* stream, void* b0, void* b1,
@@ -298,6 +298,25 @@ extern "C" int lb_observables(lb_handle* h, double* rho, double* u, double* stre
     stress[1] = (h->p.boundary == LB_COUETTE) ? h->h_out[5] / h->nx : 0.0;
     stress[2] = (h->p.boundary == LB_COUETTE) ? h->h_out[6] / h->nx : 0.0;
   }
+  return LB_OK;
+}
+
+extern "C" int lb_shear_diagnostics(lb_handle* h, double* u_k, double* i_ab) {
+  if (!h) return LB_EINVAL;
+  const size_t n = (size_t)h->nx * h->ny;
+  int rc = ensure_stage(h, 4 * n * sizeof(double));
+  if (rc) return rc;
+  const int k = h->p.k_kolmo >= 1 ? h->p.k_kolmo : 1;
+  if (launch_fields(h->p.storage, h->buf[h->cur], h->g, h->ph, h->d_stage, h->stream) !=
+          cudaSuccess ||
+      launch_shear(h->d_stage, h->g, k, h->d_partials, h->partial_cap * NOBS / 2, h->d_out,
+                   h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(h->h_out, h->d_out, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                      h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return LB_ECUDA;
+  if (u_k) *u_k = h->h_out[0];
+  if (i_ab) *i_ab = h->h_out[1];
   return LB_OK;
 }
 

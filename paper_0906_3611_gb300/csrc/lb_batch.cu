@@ -4,6 +4,7 @@
 // can be added and removed between runs (the serving loop admits requests as
 // slots and memory free up), each with its own couplings, seed and step
 // budget; a replica whose budget is spent stops inside the replayed steps.
+#include <math.h>
 #include <stddef.h>
 #include <string.h>
 
@@ -74,6 +75,7 @@ static int validate_rep(const lb_batch* b, int nx, int ny, const lb_params* p, G
   if (!(p->tau[0] > 0.5) || !(p->tau[1] > 0.5) || !(p->rho0 > 0.0)) return LB_EINVAL;
   if (p->boundary != LB_PERIODIC && p->boundary != LB_COUETTE) return LB_EINVAL;
   if (p->init_kind != LB_INIT_UNIFORM_NOISE && p->init_kind != LB_INIT_BERNOULLI) return LB_EINVAL;
+  if (!isfinite(p->g_kolmo) || (p->g_kolmo != 0.0 && p->k_kolmo < 1)) return LB_EINVAL;
   g->nx = nx;
   g->ny = ny;
   g->pitch = (nx + 31) / 32 * 32;
@@ -84,8 +86,7 @@ static int validate_rep(const lb_batch* b, int nx, int ny, const lb_params* p, G
 }
 
 static void fill_physd(const lb_params& p, PhysD* d) {
-  *d = physd_from_params(p.storage, p.tau, p.rho0, p.G_AB, p.Ga, p.Gr, p.boundary, p.U_wall,
-                         p.rho_ref);
+  *d = physd_from_params(p);
 }
 
 static void drop_graph(lb_batch* b);

@@ -3,8 +3,8 @@
 // codecs and the per-launch argument blocks.
 //
 // Arithmetic is carried in "deviation" variables d_i = f_i - w_i rho_ref,s.
-// For plain FP64/FP32 storage rho_ref = 0 and d_i = f_i; for the 16-bit
-// storages the stored value is d_i itself.  Since sum_i w_i = 1 and
+// For FP64 storage rho_ref = 0 and d_i = f_i; every other storage holds d_i
+// itself.  Since sum_i w_i = 1 and
 // sum_i w_i c_i = 0, rho_s = rho_ref,s + sum_i d_i and the momentum is
 // sum_i d_i c_i, and the BGK update of Eq. (be) reads
 //   d*_i = d_i + (1/tau_s) (w_i (drho_s + rho_s q_i) - d_i),
@@ -96,7 +96,25 @@ struct Phys {
   C W2psi[2][3]; // twice the weights of groups |c|^2 = 4, 5, 8 (the x-offset 2 terms)
   C gw[2];       // (G_AB/rho0^2) w for |c|^2 = 1, 2 (inter-species term)
   C Uwall;       // Couette wall speed
+  C gk;          // Kolmogorov body acceleration amplitude (0: off)
+  C kk;          // its wave number
 };
+
+template <typename C>
+__device__ __forceinline__ C sinpi_c(C x);
+template <>
+__device__ __forceinline__ float sinpi_c<float>(float x) { return sinpif(x); }
+template <>
+__device__ __forceinline__ double sinpi_c<double>(double x) { return sinpi(x); }
+
+// Kolmogorov body acceleration of row y: gk sin(2 pi kk y / ny) (Sec. VII),
+// with the angle reduced exactly in integers.
+template <typename C>
+__device__ __forceinline__ C body_accel(const Phys<C>& ph, int y, int ny) {
+  if (ph.gk == C(0)) return C(0);
+  const long long m = (2LL * (long long)ph.kk * y) % (2LL * ny);
+  return ph.gk * sinpi_c<C>((C)m / (C)ny);
+}
 
 // Device layout of a population buffer: one plane per D2Q9 direction i, rows
 // of `pitch` sites, and the two species of a site side by side, so that

@@ -13,6 +13,8 @@ namespace lbk {
 // Physics constants in FP64, as prepared by the API layer from lb_params.
 struct PhysD {
   double tau[2], omega[2], rho0, G_AB, Ga[2], Gr[2], U, rho_ref[2], E[2];
+  double gk;  // Kolmogorov body acceleration amplitude
+  int kk;     // its wave number
   int dev;  // 1 for the deviation storages (every storage but FP64)
 };
 
@@ -21,7 +23,8 @@ struct PhysD {
 // plain populations).  FP64 stores plain populations.
 inline PhysD physd_from_params(int storage, const double tau[2], double rho0, double G_AB,
                                const double Ga[2], const double Gr[2], int boundary,
-                               double U_wall, const double rho_ref[2]) {
+                               double U_wall, const double rho_ref[2], double g_kolmo,
+                               int k_kolmo) {
   PhysD d;
   const bool dev = (storage != LB_F64);
   d.dev = dev ? 1 : 0;
@@ -38,7 +41,13 @@ inline PhysD physd_from_params(int storage, const double tau[2], double rho0, do
   d.rho0 = rho0;
   d.G_AB = G_AB;
   d.U = (boundary == LB_COUETTE) ? U_wall : 0.0;
+  d.gk = g_kolmo;
+  d.kk = g_kolmo != 0.0 ? k_kolmo : 0;
   return d;
+}
+inline PhysD physd_from_params(const lb_params& p) {
+  return physd_from_params(p.storage, p.tau, p.rho0, p.G_AB, p.Ga, p.Gr, p.boundary, p.U_wall,
+                           p.rho_ref, p.g_kolmo, p.k_kolmo);
 }
 
 // Number of FP64 observables accumulated per block by the observe kernels:
@@ -57,6 +66,12 @@ cudaError_t launch_observe(int storage, const void* src, const Geom& g, const Ph
                            Status* status, double* partials, int cap_blocks, double* out,
                            cudaStream_t st);
 int observe_blocks(const Geom& g);
+
+// Shear diagnostics of FP64 fields (as launch_fields writes them) at wave
+// number k: out[0] = U_k, out[1] = I_AB (Sec. VII).  `partials` holds
+// 2 * cap_blocks doubles.
+cudaError_t launch_shear(const double* fields, const Geom& g, int k, double* partials,
+                         int cap_blocks, double* out, cudaStream_t st);
 
 // Fields rho_A, rho_B, u_x, u_y (FP64, [4][ny][nx]) of a state.
 cudaError_t launch_fields(int storage, const void* src, const Geom& g, const PhysD& ph,
@@ -109,6 +124,8 @@ inline Phys<C> make_phys(const PhysD& d) {
   p.gw[0] = (C)(g * table_w(0));
   p.gw[1] = (C)(g * table_w(1));
   p.Uwall = (C)d.U;
+  p.gk = (C)d.gk;
+  p.kk = (C)d.kk;
   return p;
 }
 

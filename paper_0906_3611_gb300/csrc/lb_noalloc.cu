@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(NA_THREADS)
       drho[s] = a;
       rho[s] = ph.rho_ref[s] + a;
     }
+    const C gb = body_accel(ph, y, g.ny);  // Kolmogorov body acceleration of the row
     C Fx[2], Fy[2];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(NA_THREADS)
           }
         }
       const C pc = s_psi[s][ty + 2][tx + 2];
-      Fx[s] = -pc * sx - rho[s] * xx;
+      Fx[s] = -pc * sx - rho[s] * xx + rho[s] * gb;
       Fy[s] = -pc * sy - rho[s] * xy;
     }
     C jx[2], jy[2];
@@ -253,8 +254,7 @@ extern "C" int lb_observables_noalloc(const void* f, int nx, int ny, int pitch, 
   g.pitch = pitch;
   g.boundary = p->boundary;
   g.plane = (long long)ny * pitch;
-  const PhysD d = physd_from_params(p->storage, p->tau, p->rho0, p->G_AB, p->Ga, p->Gr,
-                                    p->boundary, p->U_wall, p->rho_ref);
+  const PhysD d = physd_from_params(*p);
 
   // the status counter must start at zero; every partial record is overwritten
   if (cudaMemsetAsync(scratch + kStatusSlot, 0, sizeof(double), st) != cudaSuccess) return LB_ECUDA;

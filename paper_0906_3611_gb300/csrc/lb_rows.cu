@@ -452,7 +452,8 @@ struct RowsLoop {
     if (COLLIDE) {
       // ---- row o = r - 2 (staged row q - 2) is complete: collide and push ----
       P d[9], rho;
-      relax(sm.stage + slot_of(q - 2) * SLOT + SOFF + t, Sx0, Sy0, Cx0, Cy0, drho0, psi0, d, rho);
+      relax(sm.stage + slot_of(q - 2) * SLOT + SOFF + t, Sx0, Sy0, Cx0, Cy0, drho0, psi0,
+            body_accel(ph, ylo + q - 4, g.ny), d, rho);
       cur = row_values(jn);
       if (active) push(ylo + q - 4, d, rho, drho0);
     } else {
@@ -494,8 +495,8 @@ struct RowsLoop {
         // ---- row o = r - 2 (staged row q - 2) is complete: collide and push ----
         if (q >= 4 && active) {
           P d[9], rho;
-          relax(sm.stage + slot_of(q - 2) * SLOT + SOFF + t, Sx0, Sy0, Cx0, Cy0, drho0, psi0, d,
-                rho);
+          relax(sm.stage + slot_of(q - 2) * SLOT + SOFF + t, Sx0, Sy0, Cx0, Cy0, drho0, psi0,
+                body_accel(ph, ylo + q - 4, g.ny), d, rho);
           push(ylo + q - 4, d, rho, drho0);
         }
         // the warp is done with staged row q - 2
@@ -540,7 +541,7 @@ struct RowsLoop {
   // staged row): d[] becomes f*_i - w_i rho_ref (mass-exact rest population
   // for the rounded storages); rho is the site's density pair.
   __device__ __forceinline__ void relax(const T2* orow, P Sx0, P Sy0, P Cx0, P Cy0, P& drho,
-                                        P psi0, P (&d)[9], P& rho_out) {
+                                        P psi0, C gb, P (&d)[9], P& rho_out) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) d[i] = PS::ld(orow[i * SW]);
     if (!RowsCfg<STORAGE>::LAG) {  // the row's drho and psi, as its staging formed them
@@ -549,8 +550,8 @@ struct RowsLoop {
     }
     const P rho = padd(rho_ref, drho);
     rho_out = rho;
-    // G = -F: F_s = -psi_s S_s - rho_s C_s
-    const P Gx = pfma(psi0, Sx0, pmul(rho, Cx0));
+    // G = -F: F_s = -psi_s S_s - rho_s C_s (+ rho_s gb along x, the body force)
+    const P Gx = pfma(rho, pbc(-gb), pfma(psi0, Sx0, pmul(rho, Cx0)));
     const P Gy = pfma(psi0, Sy0, pmul(rho, Cy0));
     const P jx = padd(padd(psub(d[1], d[3]), psub(d[5], d[6])), psub(d[8], d[7]));
     const P jy = padd(padd(psub(d[2], d[4]), psub(d[5], d[8])), psub(d[6], d[7]));

@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(TTHREADS)
     }
 
     // -- force, Eq. (FORCE): psi stencil over both belts, rho stencil on belt 1 --
+    const C gb = body_accel(ph, y, g.ny);
     C Fx[2], Fy[2];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(TTHREADS)
           }
         }
       const C pc = s_psi[s][ty + 2][tx + 2];
-      Fx[s] = -pc * sx - rho[s] * xx;
+      Fx[s] = -pc * sx - rho[s] * xx + rho[s] * gb;  // (+ the Kolmogorov body force)
       Fy[s] = -pc * sy - rho[s] * xy;
     }
 
@@ -278,6 +279,67 @@ __global__ void __launch_bounds__(256)
     out[2 * n + site] = (double)((jx[0] * ph.omega[0] + jx[1] * ph.omega[1]) / den);
     out[3 * n + site] = (double)((jy[0] * ph.omega[0] + jy[1] * ph.omega[1]) / den);
   }
+}
+
+// Shear diagnostics (Sec. VII) of FP64 fields [rho_A, rho_B, u_x, u_y][ny][nx]:
+// per block, sum u_x sin(2 pi k y / ny) and -grad rho_A . grad rho_B (central
+// differences, periodic in x, stencil rows in y), then one block sums the
+// blocks in a fixed order.
+__global__ void __launch_bounds__(256) k_shear_partials(const double* __restrict__ fields, Geom g,
+                                                        int k, double* __restrict__ partials) {
+  const long long n = (long long)g.nx * g.ny;
+  double su = 0.0, si = 0.0;
+  for (long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x; site < n;
+       site += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(site / g.nx), x = (int)(site % g.nx);
+    const long long m = (2LL * k * y) % (2LL * g.ny);
+    su += fields[2 * n + site] * sinpi((double)m / (double)g.ny);
+    const int xm = wrapi(x - 1, g.nx), xp = wrapi(x + 1, g.nx);
+    const int ym = stencil_row(y - 1, g.ny, g.boundary), yp = stencil_row(y + 1, g.ny, g.boundary);
+    double gx[2], gy[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const double* r = fields + s * n;
+      gx[s] = 0.5 * (r[(long long)y * g.nx + xp] - r[(long long)y * g.nx + xm]);
+      gy[s] = 0.5 * (r[(long long)yp * g.nx + x] - r[(long long)ym * g.nx + x]);
+    }
+    si -= gx[0] * gx[1] + gy[0] * gy[1];
+  }
+  __shared__ double red[2][256];
+  red[0][threadIdx.x] = su;
+  red[1][threadIdx.x] = si;
+  __syncthreads();
+  for (int stride = 128; stride > 0; stride >>= 1) {
+    if ((int)threadIdx.x < stride) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + stride];
+      red[1][threadIdx.x] += red[1][threadIdx.x + stride];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 2) partials[2 * blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(32) k_shear_finalize(const double* __restrict__ partials,
+                                                       int nblocks, Geom g, double* out) {
+  if (threadIdx.x != 0) return;
+  double su = 0.0, si = 0.0;
+  for (int b = 0; b < nblocks; ++b) {
+    su += partials[2 * b];
+    si += partials[2 * b + 1];
+  }
+  out[0] = 2.0 * su / ((double)g.nx * (double)g.ny);  // U_k
+  out[1] = si;                                        // I_AB
+}
+
+cudaError_t launch_shear(const double* fields, const Geom& g, int k, double* partials,
+                         int cap_blocks, double* out, cudaStream_t st) {
+  const long long n = (long long)g.nx * g.ny;
+  long long nb = (n + 255) / 256;
+  if (nb > cap_blocks) nb = cap_blocks;
+  if (nb < 1) nb = 1;
+  k_shear_partials<<<(unsigned)nb, 256, 0, st>>>(fields, g, k, partials);
+  k_shear_finalize<<<1, 32, 0, st>>>(partials, (int)nb, g, out);
+  return cudaGetLastError();
 }
 
 // ---- launchers ----

@@ -24,7 +24,8 @@ ELEM_BYTES = {LB_F64: 8, LB_F32: 4, LB_BF16_DEV: 2, LB_F16_DEV: 2}
 
 # every entry point declared in include/lb.h
 EXPORTED = ["lb_state_bytes", "lb_create", "lb_create_on", "lb_init_random", "lb_step",
-            "lb_observables", "lb_get_state", "lb_set_state", "lb_set_state_raw",
+            "lb_observables", "lb_shear_diagnostics", "lb_get_state", "lb_set_state",
+            "lb_set_state_raw",
             "lb_get_state_raw", "lb_time", "lb_status", "lb_sync", "lb_destroy", "lb_strerror",
             "lb_observables_noalloc", "lb_batch_create", "lb_batch_add", "lb_batch_remove",
             "lb_batch_set_steps", "lb_batch_run", "lb_batch_poll", "lb_batch_observables",
@@ -36,7 +37,8 @@ class lb_params(ctypes.Structure):
                 ("Ga", ctypes.c_double * 2), ("Gr", ctypes.c_double * 2), ("boundary", ctypes.c_int),
                 ("U_wall", ctypes.c_double), ("storage", ctypes.c_int),
                 ("rho_ref", ctypes.c_double * 2), ("init_kind", ctypes.c_int),
-                ("init", ctypes.c_double * 6)]
+                ("init", ctypes.c_double * 6), ("g_kolmo", ctypes.c_double),
+                ("k_kolmo", ctypes.c_int)]
 
 
 class LBError(RuntimeError):
@@ -61,6 +63,7 @@ def _load():
         "lb_init_random": (ctypes.c_int, [vp, ctypes.c_uint64]),
         "lb_step": (ctypes.c_int, [vp, ctypes.c_int64]),
         "lb_observables": (ctypes.c_int, [vp, dp, dp, dp, dp]),
+        "lb_shear_diagnostics": (ctypes.c_int, [vp, dp, dp]),
         "lb_get_state": (ctypes.c_int, [vp, dp]),
         "lb_set_state": (ctypes.c_int, [vp, dp]),
         "lb_set_state_raw": (ctypes.c_int, [vp, vp]),
@@ -110,7 +113,8 @@ def _check(rc: int, what: str):
 
 def make_params(tau=(1.0, 1.0), rho0=0.7, G_AB=0.405, Ga=(-9.0, -9.0), Gr=(8.1, 8.1),
                 boundary=LB_PERIODIC, U_wall=0.0, storage=LB_F32, rho_ref=(1.0, 1.0),
-                init_kind=LB_INIT_UNIFORM_NOISE, init=(1.0, 1.0, 0.05)) -> lb_params:
+                init_kind=LB_INIT_UNIFORM_NOISE, init=(1.0, 1.0, 0.05), g_kolmo=0.0,
+                k_kolmo=1) -> lb_params:
     p = lb_params()
     p.tau[:] = list(tau)
     p.rho0 = rho0
@@ -124,6 +128,8 @@ def make_params(tau=(1.0, 1.0), rho0=0.7, G_AB=0.405, Ga=(-9.0, -9.0), Gr=(8.1, 
     p.init_kind = init_kind
     iv = list(init) + [0.0] * (6 - len(init))
     p.init[:] = iv
+    p.g_kolmo = g_kolmo
+    p.k_kolmo = k_kolmo
     return p
 
 
@@ -159,6 +165,14 @@ def lb_step(h: int, n: int) -> None:
 
 def lb_observables(h: int, rho=None, u=None, stress=None, mass=None) -> None:
     _check(_lib.lb_observables(h, _dp(rho), _dp(u), _dp(stress), _dp(mass)), "lb_observables")
+
+
+def lb_shear_diagnostics(h: int) -> tuple[float, float]:
+    """(U_k, I_AB) of the current state (Sec. VII)."""
+    uk = np.zeros(1)
+    iab = np.zeros(1)
+    _check(_lib.lb_shear_diagnostics(h, _dp(uk), _dp(iab)), "lb_shear_diagnostics")
+    return float(uk[0]), float(iab[0])
 
 
 def lb_get_state(h: int, f: np.ndarray) -> None:
@@ -299,6 +313,11 @@ class Lattice:
     def step(self, n: int = 1):
         lb_step(self.h, n)
         return self
+
+    def shear_diagnostics(self) -> dict:
+        """U_k (R = U_k / U0, Eq. (RESPONSE)) and I_AB (Eq. (INDICATOR))."""
+        uk, iab = lb_shear_diagnostics(self.h)
+        return {"U_k": uk, "I_AB": iab}
 
     def observables(self, fields: bool = False) -> dict:
         stress = np.zeros(3)

@@ -1,0 +1,116 @@
+"""Kolmogorov shear (Sec. VII) on the GPU, against the FP64 oracle.
+
+* One step with the body force: FP64 1e-12 (both step kernels, periodic and
+  Couette lattices, the paper's rho0 = 0.7 standard couplings), FP32 1e-5.
+* Without couplings the GPU reaches the oracle's pinned Kolmogorov flow:
+  U_k + g/2 = g / (nu k^2) to fourth order at tau = 1.
+* lb_shear_diagnostics equals the oracle's diagnostics of the same state
+  (U_k and I_AB to 1e-12 for FP64 storage).
+* A batched replica with the body force equals the lattice run alone.
+"""
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+W9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+# Eq. (STANDARD07): rho0 = 0.7, (Ga, Gr) = (-15, 14.1) for A and (-14, 13.1) for B
+STD07 = dict(tau=(1.0, 1.0), rho0=0.7, G_AB=0.405, Ga=(-15.0, -14.0), Gr=(14.1, 13.1))
+
+
+@pytest.fixture(scope="module")
+def lb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0906_3611_gb300 import lb as _lb
+    return _lb
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b) / np.abs(b)))
+
+
+@pytest.mark.parametrize("kernel", ["rows", "tile"])
+@pytest.mark.parametrize("boundary,U", [(0, 0.0), (1, 0.02)])
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_one_step_with_the_body_force(lb, monkeypatch, kernel, boundary, U, storage, tol):
+    st = {"f64": lb.LB_F64, "f32": lb.LB_F32}[storage]
+    monkeypatch.setenv("LB_STEP_KERNEL", kernel)
+    nx, ny, g, k = 264, 40, 2e-3, 3
+    f = inputs.populations(nx, ny, seed=21, base=W9, rel_amp=0.05, species_scale=(0.6, 0.62))
+    if storage == "f32":
+        f = f.astype(np.float32).astype(np.float64)
+    p = lb.make_params(**STD07, boundary=boundary, U_wall=U, storage=st, rho_ref=(0.6, 0.62),
+                       g_kolmo=g, k_kolmo=k)
+    lat = lb.Lattice(nx, ny, p)
+    out = lat.set_state(f).step(1).get_state()
+    assert lat.status() == lb.LB_OK
+    lat.close()
+    ref, bad = oracle.step(f, dict(STD07, boundary=boundary, U_wall=U, g_kolmo=g, k_kolmo=k), 1)
+    assert bad == 0
+    assert _rel(out, ref) <= tol
+    # the force mattered: without it the step differs by far more than the tolerance
+    ref0, _ = oracle.step(f, dict(STD07, boundary=boundary, U_wall=U), 1)
+    assert _rel(ref0, ref) > 100 * tol
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-9), ("f32", 1e-5)])
+def test_kolmogorov_flow_without_couplings(lb, storage, tol):
+    st = {"f64": lb.LB_F64, "f32": lb.LB_F32}[storage]
+    ny, nx, g = 32, 128, 1e-6
+    p = lb.make_params(tau=(1.0, 1.0), rho0=1.0, G_AB=0.0, Ga=(0.0, 0.0), Gr=(0.0, 0.0),
+                       storage=st, rho_ref=(1.0, 1.0), g_kolmo=g, k_kolmo=1)
+    lat = lb.Lattice(nx, ny, p)
+    lat.set_state(np.ones((2, 1, ny, nx)) * W9[None, :, None, None])
+    nu, k = 0.5 / 3.0, 2 * np.pi / ny
+    lat.step(int(20 / (nu * k * k)))
+    uk = lat.shear_diagnostics()["U_k"]
+    assert lat.status() == lb.LB_OK
+    lat.close()
+    # the oracle's pinned value at this size (fourth-order lattice error, 6.2e-6)
+    ref = 6.2e-6
+    assert (uk + g / 2) / (g / (nu * k * k)) - 1 == pytest.approx(ref, abs=max(tol, 2e-7))
+
+
+@pytest.mark.parametrize("boundary", [0, 1])
+def test_shear_diagnostics_match_the_oracle(lb, boundary):
+    nx, ny = 136, 48
+    pd = dict(STD07, boundary=boundary, U_wall=0.01 * boundary, g_kolmo=1e-4, k_kolmo=1)
+    p = lb.make_params(**STD07, boundary=boundary, U_wall=0.01 * boundary, storage=lb.LB_F64,
+                       rho_ref=(0.6, 0.6), init_kind=lb.LB_INIT_UNIFORM_NOISE,
+                       init=(0.612, 0.612, 0.01), g_kolmo=1e-4, k_kolmo=1)
+    lat = lb.Lattice(nx, ny, p).init_random(4).step(300)
+    d = lat.shear_diagnostics()
+    f = lat.get_state()
+    assert lat.status() == lb.LB_OK
+    lat.close()
+    ref = oracle.shear_diagnostics(f, pd)
+    assert ref["bad"] == 0
+    assert d["U_k"] == pytest.approx(ref["U_k"], rel=1e-12)
+    assert d["I_AB"] == pytest.approx(ref["I_AB"], rel=1e-12)
+    assert abs(d["U_k"]) > 0 and d["I_AB"] > 0  # flowing; interfaces present
+
+
+def test_batched_kolmogorov_replicas_equal_the_lattice_alone(lb, monkeypatch):
+    p1 = lb.make_params(**STD07, storage=lb.LB_F32, rho_ref=(0.612, 0.612),
+                        init_kind=lb.LB_INIT_UNIFORM_NOISE, init=(0.612, 0.612, 0.01),
+                        g_kolmo=2e-5, k_kolmo=1)
+    p2 = lb.make_params(**STD07, storage=lb.LB_F32, rho_ref=(0.612, 0.612),
+                        init_kind=lb.LB_INIT_UNIFORM_NOISE, init=(0.612, 0.612, 0.01),
+                        g_kolmo=6e-5, k_kolmo=2)
+    b = lb.Batch(4, lb.LB_F32)
+    s1 = b.add(128, 128, p1, 1, 40)
+    s2 = b.add(256, 64, p2, 2, 40)
+    b.run(40)
+    assert b.status() == lb.LB_OK
+    got = [b.get_state(s1), b.get_state(s2)]
+    b.close()
+    monkeypatch.setenv("LB_STEP_KERNEL", "rows")
+    for (nx, ny, p, seed), g in zip([(128, 128, p1, 1), (256, 64, p2, 2)], got):
+        lat = lb.Lattice(nx, ny, p).init_random(seed).step(40)
+        assert np.array_equal(lat.get_state(), g)
+        lat.close()
