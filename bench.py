@@ -45,6 +45,13 @@ BATCHES = {
     "batch256_f32": (256, (128, 256, 512, 1024), 0.05, 1),
     "batch256_f16dev": (256, (128, 256, 512, 1024), 0.05, 3),
 }
+SHEARS = {
+    # name: (replicas, side, U0 (laminar amplitude of the Kolmogorov flow), storage)
+    # the paper's shear ensemble (Sec. VII-VIII): 128^2 lattices, rho0 = 0.7 standard
+    # couplings, <rho> = 0.612 +- 0.01, body force g = U0 nu k^2 at k = 2 pi / 128
+    "shear100x128_f32": (100, 128, 0.03, 1),
+}
+STD07 = dict(tau=(1.0, 1.0), rho0=0.7, G_AB=0.405, Ga=(-15.0, -14.0), Gr=(14.1, 13.1))
 SERVES = {
     # name: (storage, requests, rate per s, sides, steps range, HBM budget, slots, chunk)
     "serve_f32": (1, 48, 50.0, tuple(range(64, 2049, 64)), (1e3, 1e5), 150e9, 64, 256),
@@ -424,6 +431,79 @@ def run_batch(args):
     D.close()
 
 
+def run_shear(args):
+    """Ensemble of Kolmogorov-sheared lattices in one batch; the response R = U_k / U0
+    of every replica after the timed steps gives the ensemble mean and kurtosis."""
+    import numpy as np
+    import torch
+
+    from paper_0906_3611_gb300 import lb
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    D = Dist()
+    n, side, U0, storage = SHEARS[args.workload]
+    nu, k = (STD07["tau"][0] - 0.5) / 3.0, 2.0 * np.pi / side
+    g = U0 * nu * k * k
+    stream = torch.cuda.Stream()
+    p = lb.make_params(**STD07, storage=storage, rho_ref=(0.612, 0.612),
+                       init_kind=lb.LB_INIT_UNIFORM_NOISE, init=(0.612, 0.612, 0.01),
+                       g_kolmo=g, k_kolmo=1)
+    b = lb.Batch(n, storage, stream)
+    for r in range(n):
+        b.add(side, side, p, 1000 * rank + r, args.warmup + args.steps + 64)
+    layout, rows = b.autotune(2)
+    for r in range(n):
+        b.set_steps(r, args.warmup + args.steps)
+    sampler = ClockSampler(local)
+    sampler.start()
+    b.run(args.warmup)
+    stream.synchronize()
+    D.barrier()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    b.run(args.steps)
+    end.record(stream)
+    end.synchronize()
+    D.barrier()
+    clocks = sampler.stop()
+    ms = start.elapsed_time(end)
+    status = b.status()
+    diag = [b.shear_diagnostics(r) for r in range(n)]
+    b.close()
+    R = np.array(D.gather([d["U_k"] / U0 for d in diag]))
+    iab = np.array(D.gather([d["I_AB"] for d in diag]))
+    sites = n * side * side
+    ms_max = D.max(ms)
+    value = whole_job_mlups(D.sum(sites * args.steps), ms_max * 1e-3)
+    es = ELEM[storage]
+    achieved = 2 * 18 * es * sites / (ms * 1e-3 / args.steps) / 1e9
+    peak, peak_kind = peaks()
+    if rank == 0:
+        line = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": args.workload, "replicas": n, "side": side,
+                           "couplings": "rho0 = 0.7 standard set", "U0": U0, "g_kolmo": g,
+                           "storage": STORAGE_NAME[storage],
+                           "work_list": {"layout": ["contiguous", "packed"][layout],
+                                         "max_piece_rows": rows},
+                           "l2": f"{sites * 18 * es / 1e6:.0f} MB read per step: partly "
+                                 "L2-resident (129 MB L2); not a bandwidth headline"},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": None,
+                             "bytes_per_site": 2 * 18 * es, "peak_kind": peak_kind},
+                "response": {"t": args.warmup + args.steps, "R_mean": float(R.mean()),
+                             "R_kurtosis": float(np.mean(R ** 4) / np.mean(R ** 2) ** 2),
+                             "I_AB_mean": float(iab.mean())},
+                "gpu_launches": args.steps, "clocks": clocks,
+                "status": lb.lb_strerror(status), "impl": "gb300"}
+        print(json.dumps(line), flush=True)
+    D.close()
+
+
 def run_serve(args):
     """Serving loop: Poisson arrivals of simulation requests, continuous batching."""
     import numpy as np
@@ -484,7 +564,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="couette4096_f32",
-                    choices=sorted(WORKLOADS) + sorted(BATCHES) + sorted(SERVES))
+                    choices=sorted(WORKLOADS) + sorted(BATCHES) + sorted(SHEARS) + sorted(SERVES))
     ap.add_argument("--requests", type=int, default=0)
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -495,6 +575,8 @@ def main():
         run_reference(args)
     elif args.workload in BATCHES:
         run_batch(args)
+    elif args.workload in SHEARS:
+        run_shear(args)
     elif args.workload in SERVES:
         run_serve(args)
     else:

@@ -267,6 +267,8 @@ LB_API int lb_batch_poll(lb_batch *b, int64_t *remaining, int64_t *steps_done);
 LB_API int lb_batch_observables(lb_batch *b, int slot, double *rho, double *u, double *stress,
                                 double *mass);
 LB_API int lb_batch_get_state(lb_batch *b, int slot, double *f);
+/* lb_shear_diagnostics of one replica (synchronises). */
+LB_API int lb_batch_shear_diagnostics(lb_batch *b, int slot, double *u_k, double *i_ab);
 
 /* Pick the work-list layout and piece length that time fastest on the
  * current replicas, among five candidates: layout 0 deals the strip-rows of

@@ -567,6 +567,39 @@ static int ensure_stage_b(lb_batch* b, size_t bytes) {
   return LB_OK;
 }
 
+extern "C" int lb_batch_shear_diagnostics(lb_batch* b, int slot, double* u_k, double* i_ab) {
+  if (!b || slot < 0 || slot >= b->capacity || !b->slots[slot].used) return LB_EINVAL;
+  const Slot& s = b->slots[slot];
+  void* cur = nullptr;
+  int rc = current_buffer(b, slot, &cur);
+  if (rc) return rc;
+  const size_t n = (size_t)s.nx * s.ny;
+  rc = ensure_stage_b(b, 4 * n * sizeof(double));
+  if (rc) return rc;
+  const int nb = observe_blocks(s.g);
+  if (nb > b->partial_cap) {
+    cudaFree(b->d_partials);
+    b->d_partials = nullptr;
+    b->partial_cap = 0;
+    if (cudaMalloc(&b->d_partials, (size_t)nb * NOBS * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return LB_ENOMEM;
+    }
+    b->partial_cap = nb;
+  }
+  const int k = s.p.k_kolmo >= 1 ? s.p.k_kolmo : 1;
+  if (launch_fields(s.p.storage, cur, s.g, s.ph, b->d_stage, b->stream) != cudaSuccess ||
+      launch_shear(b->d_stage, s.g, k, b->d_partials, b->partial_cap * NOBS / 2, b->d_out,
+                   b->stream) != cudaSuccess ||
+      cudaMemcpyAsync(b->h_out, b->d_out, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                      b->stream) != cudaSuccess ||
+      cudaStreamSynchronize(b->stream) != cudaSuccess)
+    return LB_ECUDA;
+  if (u_k) *u_k = b->h_out[0];
+  if (i_ab) *i_ab = b->h_out[1];
+  return LB_OK;
+}
+
 extern "C" int lb_batch_observables(lb_batch* b, int slot, double* rho, double* u, double* stress,
                                     double* mass) {
   if (!b || slot < 0 || slot >= b->capacity || !b->slots[slot].used) return LB_EINVAL;

@@ -29,7 +29,8 @@ EXPORTED = ["lb_state_bytes", "lb_create", "lb_create_on", "lb_init_random", "lb
             "lb_get_state_raw", "lb_time", "lb_status", "lb_sync", "lb_destroy", "lb_strerror",
             "lb_observables_noalloc", "lb_batch_create", "lb_batch_add", "lb_batch_remove",
             "lb_batch_set_steps", "lb_batch_run", "lb_batch_poll", "lb_batch_observables",
-            "lb_batch_get_state", "lb_batch_autotune", "lb_batch_status", "lb_batch_destroy"]
+            "lb_batch_get_state", "lb_batch_shear_diagnostics", "lb_batch_autotune",
+            "lb_batch_status", "lb_batch_destroy"]
 
 
 class lb_params(ctypes.Structure):
@@ -84,6 +85,7 @@ def _load():
         "lb_batch_poll": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
         "lb_batch_observables": (ctypes.c_int, [vp, ctypes.c_int, dp, dp, dp, dp]),
         "lb_batch_get_state": (ctypes.c_int, [vp, ctypes.c_int, dp]),
+        "lb_batch_shear_diagnostics": (ctypes.c_int, [vp, ctypes.c_int, dp, dp]),
         "lb_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                              ctypes.POINTER(ctypes.c_int)]),
         "lb_batch_status": (ctypes.c_int, [vp]),
@@ -260,6 +262,13 @@ def lb_batch_get_state(b: int, slot: int, f: np.ndarray) -> None:
     _check(_lib.lb_batch_get_state(b, slot, _dp(f)), "lb_batch_get_state")
 
 
+def lb_batch_shear_diagnostics(b: int, slot: int) -> tuple[float, float]:
+    uk = np.zeros(1)
+    iab = np.zeros(1)
+    _check(_lib.lb_batch_shear_diagnostics(b, slot, _dp(uk), _dp(iab)), "lb_batch_shear_diagnostics")
+    return float(uk[0]), float(iab[0])
+
+
 def lb_batch_autotune(b: int, steps_per_candidate: int) -> tuple[int, int]:
     layout = ctypes.c_int(0)
     rows = ctypes.c_int(0)
@@ -413,6 +422,10 @@ class Batch:
         f = np.empty((2, 9, ny, nx))
         lb_batch_get_state(self.h, slot, f)
         return f
+
+    def shear_diagnostics(self, slot: int) -> dict:
+        uk, iab = lb_batch_shear_diagnostics(self.h, slot)
+        return {"U_k": uk, "I_AB": iab}
 
     def autotune(self, steps_per_candidate: int = 4) -> tuple[int, int]:
         """(layout, longest piece in rows) chosen by the library's autotuner."""

@@ -108,9 +108,11 @@ def test_batched_kolmogorov_replicas_equal_the_lattice_alone(lb, monkeypatch):
     b.run(40)
     assert b.status() == lb.LB_OK
     got = [b.get_state(s1), b.get_state(s2)]
+    diag = [b.shear_diagnostics(s1), b.shear_diagnostics(s2)]
     b.close()
     monkeypatch.setenv("LB_STEP_KERNEL", "rows")
-    for (nx, ny, p, seed), g in zip([(128, 128, p1, 1), (256, 64, p2, 2)], got):
+    for (nx, ny, p, seed), g, d in zip([(128, 128, p1, 1), (256, 64, p2, 2)], got, diag):
         lat = lb.Lattice(nx, ny, p).init_random(seed).step(40)
         assert np.array_equal(lat.get_state(), g)
+        assert lat.shear_diagnostics() == d
         lat.close()
