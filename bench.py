@@ -459,6 +459,8 @@ def run_shear(args):
     sampler.start()
     b.run(args.warmup)
     stream.synchronize()
+    for r in range(n):  # the ageing snapshot phi(t_w) at t_w = warmup
+        b.phi_snapshot(r)
     D.barrier()
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
@@ -471,7 +473,9 @@ def run_shear(args):
     ms = start.elapsed_time(end)
     status = b.status()
     diag = [b.shear_diagnostics(r) for r in range(n)]
+    ov = [b.phi_overlap(r) for r in range(n)]
     b.close()
+    C = D.sum(sum(o[0] for o in ov)) / D.sum(sum(o[1] for o in ov))
     R = np.array(D.gather([d["U_k"] / U0 for d in diag]))
     iab = np.array(D.gather([d["I_AB"] for d in diag]))
     sites = n * side * side
@@ -497,7 +501,8 @@ def run_shear(args):
                              "bytes_per_site": 2 * 18 * es, "peak_kind": peak_kind},
                 "response": {"t": args.warmup + args.steps, "R_mean": float(R.mean()),
                              "R_kurtosis": float(np.mean(R ** 4) / np.mean(R ** 2) ** 2),
-                             "I_AB_mean": float(iab.mean())},
+                             "I_AB_mean": float(iab.mean()),
+                             "overlap_C": {"t_w": args.warmup, "dt_w": args.steps, "C": C}},
                 "gpu_launches": args.steps, "clocks": clocks,
                 "status": lb.lb_strerror(status), "impl": "gb300"}
         print(json.dumps(line), flush=True)

@@ -167,6 +167,16 @@ LB_API int lb_observables(lb_handle *h, double *rho, double *u, double *stress, 
  * Either pointer may be NULL. */
 LB_API int lb_shear_diagnostics(lb_handle *h, double *u_k, double *i_ab);
 
+/* Ageing overlap of Eq. (CORRE) (Sec. VII), order parameter phi = rho_A - rho_B.
+ * lb_phi_snapshot stores phi(t_w) of the current state in the handle (FP64,
+ * one device array of nx*ny doubles, kept until the next snapshot or
+ * lb_destroy).  lb_phi_overlap returns *num = sum_{x,y} phi(t_w) phi(t) and
+ * *den = sum_{x,y} phi(t_w)^2 for the current state t; C = <num>/<den>, the
+ * brackets an ensemble average the caller takes.  LB_EINVAL before the first
+ * snapshot.  Both synchronise. */
+LB_API int lb_phi_snapshot(lb_handle *h);
+LB_API int lb_phi_overlap(lb_handle *h, double *num, double *den);
+
 /* Copy the state out as FP64 (layout above); synchronises. */
 LB_API int lb_get_state(lb_handle *h, double *f);
 
@@ -267,8 +277,11 @@ LB_API int lb_batch_poll(lb_batch *b, int64_t *remaining, int64_t *steps_done);
 LB_API int lb_batch_observables(lb_batch *b, int slot, double *rho, double *u, double *stress,
                                 double *mass);
 LB_API int lb_batch_get_state(lb_batch *b, int slot, double *f);
-/* lb_shear_diagnostics of one replica (synchronises). */
+/* lb_shear_diagnostics, lb_phi_snapshot and lb_phi_overlap of one replica
+ * (synchronise; a replica's snapshot is freed with the replica). */
 LB_API int lb_batch_shear_diagnostics(lb_batch *b, int slot, double *u_k, double *i_ab);
+LB_API int lb_batch_phi_snapshot(lb_batch *b, int slot);
+LB_API int lb_batch_phi_overlap(lb_batch *b, int slot, double *num, double *den);
 
 /* Pick the work-list layout and piece length that time fastest on the
  * current replicas, among five candidates: layout 0 deals the strip-rows of

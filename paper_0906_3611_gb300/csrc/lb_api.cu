@@ -30,6 +30,7 @@ struct lb_handle {
   double* d_out = nullptr;     // NOBS reduced observables
   double* h_out = nullptr;     // pinned copy of d_out
   double* d_stage = nullptr;   // lazily allocated FP64 staging (fields / state planes)
+  double* d_phi_w = nullptr;   // ageing snapshot phi(t_w) (lazily allocated)
   size_t stage_bytes = 0;
   cudaStream_t cap_stream = nullptr;  // private stream used only for graph capture
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -170,6 +171,7 @@ extern "C" void lb_destroy(lb_handle* h) {
   cudaFree(h->d_partials);
   cudaFree(h->d_out);
   cudaFree(h->d_stage);
+  cudaFree(h->d_phi_w);
   if (h->h_out) cudaFreeHost(h->h_out);
   cudaGetLastError();
   delete h;
@@ -317,6 +319,42 @@ extern "C" int lb_shear_diagnostics(lb_handle* h, double* u_k, double* i_ab) {
     return LB_ECUDA;
   if (u_k) *u_k = h->h_out[0];
   if (i_ab) *i_ab = h->h_out[1];
+  return LB_OK;
+}
+
+extern "C" int lb_phi_snapshot(lb_handle* h) {
+  if (!h) return LB_EINVAL;
+  const size_t n = (size_t)h->nx * h->ny;
+  int rc = ensure_stage(h, 4 * n * sizeof(double));
+  if (rc) return rc;
+  if (!h->d_phi_w && cudaMalloc(&h->d_phi_w, n * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return LB_ENOMEM;
+  }
+  if (launch_fields(h->p.storage, h->buf[h->cur], h->g, h->ph, h->d_stage, h->stream) !=
+          cudaSuccess ||
+      launch_phi(h->d_stage, (long long)n, h->d_phi_w, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return LB_ECUDA;
+  return LB_OK;
+}
+
+extern "C" int lb_phi_overlap(lb_handle* h, double* num, double* den) {
+  if (!h) return LB_EINVAL;
+  if (!h->d_phi_w) return LB_EINVAL;  // no snapshot taken
+  const size_t n = (size_t)h->nx * h->ny;
+  int rc = ensure_stage(h, 4 * n * sizeof(double));
+  if (rc) return rc;
+  if (launch_fields(h->p.storage, h->buf[h->cur], h->g, h->ph, h->d_stage, h->stream) !=
+          cudaSuccess ||
+      launch_overlap(h->d_stage, h->d_phi_w, (long long)n, h->d_partials,
+                     h->partial_cap * NOBS / 2, h->d_out, h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(h->h_out, h->d_out, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                      h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return LB_ECUDA;
+  if (num) *num = h->h_out[0];
+  if (den) *den = h->h_out[1];
   return LB_OK;
 }
 

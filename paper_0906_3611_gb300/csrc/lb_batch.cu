@@ -30,6 +30,7 @@ struct Slot {
   Geom g{};
   PhysD ph{};
   void* buf[2] = {nullptr, nullptr};
+  double* phi_w = nullptr;  // ageing snapshot phi(t_w) (lazily allocated)
 };
 
 size_t rep_bytes(int storage) {
@@ -354,6 +355,7 @@ extern "C" void lb_batch_destroy(lb_batch* b) {
   for (Slot& s : b->slots) {
     cudaFree(s.buf[0]);
     cudaFree(s.buf[1]);
+    cudaFree(s.phi_w);
   }
   cudaFree(b->d_reps);
   cudaFree(b->d_items);
@@ -434,6 +436,7 @@ extern "C" int lb_batch_remove(lb_batch* b, int slot) {
   Slot& s = b->slots[slot];
   cudaFree(s.buf[0]);
   cudaFree(s.buf[1]);
+  cudaFree(s.phi_w);
   s = Slot();
   b->dirty = true;
   return LB_OK;
@@ -597,6 +600,64 @@ extern "C" int lb_batch_shear_diagnostics(lb_batch* b, int slot, double* u_k, do
     return LB_ECUDA;
   if (u_k) *u_k = b->h_out[0];
   if (i_ab) *i_ab = b->h_out[1];
+  return LB_OK;
+}
+
+static int ensure_partials_b(lb_batch* b, const Geom& g) {
+  const int nb = observe_blocks(g);
+  if (nb <= b->partial_cap) return LB_OK;
+  cudaFree(b->d_partials);
+  b->d_partials = nullptr;
+  b->partial_cap = 0;
+  if (cudaMalloc(&b->d_partials, (size_t)nb * NOBS * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return LB_ENOMEM;
+  }
+  b->partial_cap = nb;
+  return LB_OK;
+}
+
+extern "C" int lb_batch_phi_snapshot(lb_batch* b, int slot) {
+  if (!b || slot < 0 || slot >= b->capacity || !b->slots[slot].used) return LB_EINVAL;
+  Slot& s = b->slots[slot];
+  void* cur = nullptr;
+  int rc = current_buffer(b, slot, &cur);
+  if (rc) return rc;
+  const size_t n = (size_t)s.nx * s.ny;
+  rc = ensure_stage_b(b, 4 * n * sizeof(double));
+  if (rc) return rc;
+  if (!s.phi_w && cudaMalloc(&s.phi_w, n * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return LB_ENOMEM;
+  }
+  if (launch_fields(s.p.storage, cur, s.g, s.ph, b->d_stage, b->stream) != cudaSuccess ||
+      launch_phi(b->d_stage, (long long)n, s.phi_w, b->stream) != cudaSuccess ||
+      cudaStreamSynchronize(b->stream) != cudaSuccess)
+    return LB_ECUDA;
+  return LB_OK;
+}
+
+extern "C" int lb_batch_phi_overlap(lb_batch* b, int slot, double* num, double* den) {
+  if (!b || slot < 0 || slot >= b->capacity || !b->slots[slot].used) return LB_EINVAL;
+  const Slot& s = b->slots[slot];
+  if (!s.phi_w) return LB_EINVAL;  // no snapshot taken
+  void* cur = nullptr;
+  int rc = current_buffer(b, slot, &cur);
+  if (rc) return rc;
+  const size_t n = (size_t)s.nx * s.ny;
+  rc = ensure_stage_b(b, 4 * n * sizeof(double));
+  if (rc) return rc;
+  rc = ensure_partials_b(b, s.g);
+  if (rc) return rc;
+  if (launch_fields(s.p.storage, cur, s.g, s.ph, b->d_stage, b->stream) != cudaSuccess ||
+      launch_overlap(b->d_stage, s.phi_w, (long long)n, b->d_partials, b->partial_cap * NOBS / 2,
+                     b->d_out, b->stream) != cudaSuccess ||
+      cudaMemcpyAsync(b->h_out, b->d_out, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                      b->stream) != cudaSuccess ||
+      cudaStreamSynchronize(b->stream) != cudaSuccess)
+    return LB_ECUDA;
+  if (num) *num = b->h_out[0];
+  if (den) *den = b->h_out[1];
   return LB_OK;
 }
 

@@ -73,6 +73,13 @@ int observe_blocks(const Geom& g);
 cudaError_t launch_shear(const double* fields, const Geom& g, int k, double* partials,
                          int cap_blocks, double* out, cudaStream_t st);
 
+// Ageing (Eq. (CORRE)): phi = rho_A - rho_B of FP64 fields into phi[n]; and
+// out[0] = sum phi_w phi, out[1] = sum phi_w^2 for the fields' phi
+// (`partials` holds 2 * cap_blocks doubles).
+cudaError_t launch_phi(const double* fields, long long n, double* phi, cudaStream_t st);
+cudaError_t launch_overlap(const double* fields, const double* phi_w, long long n, double* partials,
+                           int cap_blocks, double* out, cudaStream_t st);
+
 // Fields rho_A, rho_B, u_x, u_y (FP64, [4][ny][nx]) of a state.
 cudaError_t launch_fields(int storage, const void* src, const Geom& g, const PhysD& ph,
                           double* fields, cudaStream_t st);

@@ -342,6 +342,73 @@ cudaError_t launch_shear(const double* fields, const Geom& g, int k, double* par
   return cudaGetLastError();
 }
 
+// Order parameter phi = rho_A - rho_B of FP64 fields (as launch_fields writes
+// them) into `phi` (the ageing snapshot of Sec. VII).
+__global__ void __launch_bounds__(256) k_phi(const double* __restrict__ fields, long long n,
+                                             double* __restrict__ phi) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    phi[i] = fields[i] - fields[n + i];
+}
+
+// Ageing overlap terms of Eq. (CORRE) for one lattice: sum phi_w phi and
+// sum phi_w^2 over the sites (block partials, then a fixed-order sum).
+__global__ void __launch_bounds__(256) k_overlap_partials(const double* __restrict__ fields,
+                                                          const double* __restrict__ phi_w,
+                                                          long long n,
+                                                          double* __restrict__ partials) {
+  double num = 0.0, den = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double w = phi_w[i];
+    num += w * (fields[i] - fields[n + i]);
+    den += w * w;
+  }
+  __shared__ double red[2][256];
+  red[0][threadIdx.x] = num;
+  red[1][threadIdx.x] = den;
+  __syncthreads();
+  for (int stride = 128; stride > 0; stride >>= 1) {
+    if ((int)threadIdx.x < stride) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + stride];
+      red[1][threadIdx.x] += red[1][threadIdx.x + stride];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 2) partials[2 * blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(32) k_pair_finalize(const double* __restrict__ partials,
+                                                      int nblocks, double* out) {
+  if (threadIdx.x != 0) return;
+  double a = 0.0, b = 0.0;
+  for (int k = 0; k < nblocks; ++k) {
+    a += partials[2 * k];
+    b += partials[2 * k + 1];
+  }
+  out[0] = a;
+  out[1] = b;
+}
+
+static int pair_blocks(long long n, int cap_blocks) {
+  long long nb = (n + 255) / 256;
+  if (nb > cap_blocks) nb = cap_blocks;
+  return nb < 1 ? 1 : (int)nb;
+}
+
+cudaError_t launch_phi(const double* fields, long long n, double* phi, cudaStream_t st) {
+  k_phi<<<pair_blocks(n, 152 * 16), 256, 0, st>>>(fields, n, phi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_overlap(const double* fields, const double* phi_w, long long n, double* partials,
+                           int cap_blocks, double* out, cudaStream_t st) {
+  const int nb = pair_blocks(n, cap_blocks);
+  k_overlap_partials<<<nb, 256, 0, st>>>(fields, phi_w, n, partials);
+  k_pair_finalize<<<1, 32, 0, st>>>(partials, nb, out);
+  return cudaGetLastError();
+}
+
 // ---- launchers ----
 
 static dim3 tile_grid(const Geom& g) { return dim3((g.nx + TTX - 1) / TTX, (g.ny + TTY - 1) / TTY); }

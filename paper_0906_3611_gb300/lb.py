@@ -24,12 +24,14 @@ ELEM_BYTES = {LB_F64: 8, LB_F32: 4, LB_BF16_DEV: 2, LB_F16_DEV: 2}
 
 # every entry point declared in include/lb.h
 EXPORTED = ["lb_state_bytes", "lb_create", "lb_create_on", "lb_init_random", "lb_step",
-            "lb_observables", "lb_shear_diagnostics", "lb_get_state", "lb_set_state",
+            "lb_observables", "lb_shear_diagnostics", "lb_phi_snapshot", "lb_phi_overlap",
+            "lb_get_state", "lb_set_state",
             "lb_set_state_raw",
             "lb_get_state_raw", "lb_time", "lb_status", "lb_sync", "lb_destroy", "lb_strerror",
             "lb_observables_noalloc", "lb_batch_create", "lb_batch_add", "lb_batch_remove",
             "lb_batch_set_steps", "lb_batch_run", "lb_batch_poll", "lb_batch_observables",
-            "lb_batch_get_state", "lb_batch_shear_diagnostics", "lb_batch_autotune",
+            "lb_batch_get_state", "lb_batch_shear_diagnostics", "lb_batch_phi_snapshot",
+            "lb_batch_phi_overlap", "lb_batch_autotune",
             "lb_batch_status", "lb_batch_destroy"]
 
 
@@ -65,6 +67,10 @@ def _load():
         "lb_step": (ctypes.c_int, [vp, ctypes.c_int64]),
         "lb_observables": (ctypes.c_int, [vp, dp, dp, dp, dp]),
         "lb_shear_diagnostics": (ctypes.c_int, [vp, dp, dp]),
+        "lb_phi_snapshot": (ctypes.c_int, [vp]),
+        "lb_phi_overlap": (ctypes.c_int, [vp, dp, dp]),
+        "lb_batch_phi_snapshot": (ctypes.c_int, [vp, ctypes.c_int]),
+        "lb_batch_phi_overlap": (ctypes.c_int, [vp, ctypes.c_int, dp, dp]),
         "lb_get_state": (ctypes.c_int, [vp, dp]),
         "lb_set_state": (ctypes.c_int, [vp, dp]),
         "lb_set_state_raw": (ctypes.c_int, [vp, vp]),
@@ -175,6 +181,28 @@ def lb_shear_diagnostics(h: int) -> tuple[float, float]:
     iab = np.zeros(1)
     _check(_lib.lb_shear_diagnostics(h, _dp(uk), _dp(iab)), "lb_shear_diagnostics")
     return float(uk[0]), float(iab[0])
+
+
+def lb_phi_snapshot(h: int) -> None:
+    _check(_lib.lb_phi_snapshot(h), "lb_phi_snapshot")
+
+
+def lb_phi_overlap(h: int) -> tuple[float, float]:
+    num = np.zeros(1)
+    den = np.zeros(1)
+    _check(_lib.lb_phi_overlap(h, _dp(num), _dp(den)), "lb_phi_overlap")
+    return float(num[0]), float(den[0])
+
+
+def lb_batch_phi_snapshot(b: int, slot: int) -> None:
+    _check(_lib.lb_batch_phi_snapshot(b, slot), "lb_batch_phi_snapshot")
+
+
+def lb_batch_phi_overlap(b: int, slot: int) -> tuple[float, float]:
+    num = np.zeros(1)
+    den = np.zeros(1)
+    _check(_lib.lb_batch_phi_overlap(b, slot, _dp(num), _dp(den)), "lb_batch_phi_overlap")
+    return float(num[0]), float(den[0])
 
 
 def lb_get_state(h: int, f: np.ndarray) -> None:
@@ -323,6 +351,15 @@ class Lattice:
         lb_step(self.h, n)
         return self
 
+    def phi_snapshot(self):
+        """Store phi(t_w) = rho_A - rho_B of the current state (Eq. (CORRE))."""
+        lb_phi_snapshot(self.h)
+        return self
+
+    def phi_overlap(self) -> tuple[float, float]:
+        """(sum phi(t_w) phi(t), sum phi(t_w)^2) for the current state t."""
+        return lb_phi_overlap(self.h)
+
     def shear_diagnostics(self) -> dict:
         """U_k (R = U_k / U0, Eq. (RESPONSE)) and I_AB (Eq. (INDICATOR))."""
         uk, iab = lb_shear_diagnostics(self.h)
@@ -426,6 +463,12 @@ class Batch:
     def shear_diagnostics(self, slot: int) -> dict:
         uk, iab = lb_batch_shear_diagnostics(self.h, slot)
         return {"U_k": uk, "I_AB": iab}
+
+    def phi_snapshot(self, slot: int):
+        lb_batch_phi_snapshot(self.h, slot)
+
+    def phi_overlap(self, slot: int) -> tuple[float, float]:
+        return lb_batch_phi_overlap(self.h, slot)
 
     def autotune(self, steps_per_candidate: int = 4) -> tuple[int, int]:
         """(layout, longest piece in rows) chosen by the library's autotuner."""

@@ -116,3 +116,43 @@ def test_batched_kolmogorov_replicas_equal_the_lattice_alone(lb, monkeypatch):
         assert np.array_equal(lat.get_state(), g)
         assert lat.shear_diagnostics() == d
         lat.close()
+
+
+def test_ageing_overlap_matches_its_definition(lb):
+    """Eq. (CORRE) terms: sum phi(t_w) phi(t) and sum phi(t_w)^2, phi = rho_A - rho_B."""
+    nx, ny = 136, 48
+    p = lb.make_params(**STD07, storage=lb.LB_F64, rho_ref=(0.6, 0.6),
+                       init_kind=lb.LB_INIT_UNIFORM_NOISE, init=(0.612, 0.612, 0.01),
+                       g_kolmo=1e-4, k_kolmo=1)
+    lat = lb.Lattice(nx, ny, p).init_random(8)
+    with pytest.raises(lb.LBError):
+        lat.phi_overlap()  # no snapshot yet
+    lat.step(200).phi_snapshot()
+    num0, den0 = lat.phi_overlap()
+    assert num0 == den0 > 0  # C(t_w, 0) = 1
+    rho_w = lat.observables(fields=True)["rho"]
+    lat.step(150)
+    num, den = lat.phi_overlap()
+    rho_t = lat.observables(fields=True)["rho"]
+    lat.close()
+    phi_w, phi_t = rho_w[0] - rho_w[1], rho_t[0] - rho_t[1]
+    assert den == pytest.approx(float(np.sum(phi_w * phi_w)), rel=1e-12)
+    assert num == pytest.approx(float(np.sum(phi_w * phi_t)), rel=1e-12)
+    assert 0.0 < num / den < 1.0  # the configuration has moved
+
+
+def test_batched_overlap_equals_the_lattice_alone(lb, monkeypatch):
+    p = lb.make_params(**STD07, storage=lb.LB_F32, rho_ref=(0.612, 0.612),
+                       init_kind=lb.LB_INIT_UNIFORM_NOISE, init=(0.612, 0.612, 0.01),
+                       g_kolmo=2e-5, k_kolmo=1)
+    b = lb.Batch(2, lb.LB_F32)
+    s = b.add(128, 128, p, 5, 60)
+    b.run(30)
+    b.phi_snapshot(s)
+    b.run(30)
+    got = b.phi_overlap(s)
+    b.close()
+    monkeypatch.setenv("LB_STEP_KERNEL", "rows")
+    lat = lb.Lattice(128, 128, p).init_random(5).step(30).phi_snapshot().step(30)
+    assert lat.phi_overlap() == got
+    lat.close()
