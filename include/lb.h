@@ -167,6 +167,19 @@ LB_API int lb_observables(lb_handle *h, double *rho, double *u, double *stress, 
  * Either pointer may be NULL. */
 LB_API int lb_shear_diagnostics(lb_handle *h, double *u_k, double *i_ab);
 
+/* Shear-response record (Sec. VII: the response R(t) and the bursts of the
+ * flow speed behind the Barkhausen statistics need it at every step).  After
+ * lb_series_start every step adds sum_{x,y} u_x sin(2 pi k y / ny) (u the
+ * common velocity of the step's collision, k = k_kolmo or 1) to a device ring
+ * of `capacity` entries, at no host synchronisation.  lb_series_read writes
+ * the most recent min(steps recorded, capacity, max) entries, oldest first,
+ * as U_k = (2 / (nx ny)) sum (so R = U_k / U0), and sets *count; it
+ * synchronises.  lb_series_stop frees the record.  A step whose kernel gave
+ * up a bounded wait (LB_ETIMEOUT) is not recorded. */
+LB_API int lb_series_start(lb_handle *h, int64_t capacity);
+LB_API int lb_series_read(lb_handle *h, double *out, int64_t max, int64_t *count);
+LB_API int lb_series_stop(lb_handle *h);
+
 /* Ageing overlap of Eq. (CORRE) (Sec. VII), order parameter phi = rho_A - rho_B.
  * lb_phi_snapshot stores phi(t_w) of the current state in the handle (FP64,
  * one device array of nx*ny doubles, kept until the next snapshot or

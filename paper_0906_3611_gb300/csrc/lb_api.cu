@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "lb.h"
 #include "lb_kernels.h"
@@ -31,11 +32,13 @@ struct lb_handle {
   double* h_out = nullptr;     // pinned copy of d_out
   double* d_stage = nullptr;   // lazily allocated FP64 staging (fields / state planes)
   double* d_phi_w = nullptr;   // ageing snapshot phi(t_w) (lazily allocated)
+  void* d_body = nullptr;      // Kolmogorov body acceleration per row (row kernel)
   size_t stage_bytes = 0;
   cudaStream_t cap_stream = nullptr;  // private stream used only for graph capture
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int graph_steps = 0;
   int use_rows = 0;       // 1 if the row-streaming kernel serves this lattice
+  Series sr{nullptr, nullptr, nullptr, 0, 0, 0u};  // shear-response record (off by default)
 };
 
 static const int kGraphSteps = 32;  // steps per captured graph (even: keeps buffer parity)
@@ -106,6 +109,11 @@ static int create_common(int nx, int ny, const lb_params* p, void* stream, void*
     }
     h->owns = true;
   }
+  if (make_body_table(p->storage, h->ph, ny, &h->d_body, h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    lb_destroy(h);
+    return LB_ENOMEM;
+  }
   h->partial_cap = observe_blocks(h->g);
   if (cudaMalloc(&h->d_status, sizeof(Status)) != cudaSuccess ||
       cudaMalloc(&h->d_partials, (size_t)h->partial_cap * NOBS * sizeof(double)) != cudaSuccess ||
@@ -172,6 +180,10 @@ extern "C" void lb_destroy(lb_handle* h) {
   cudaFree(h->d_out);
   cudaFree(h->d_stage);
   cudaFree(h->d_phi_w);
+  cudaFree(h->d_body);
+  cudaFree(h->sr.buf);
+  cudaFree(h->sr.t);
+  cudaFree(h->sr.done);
   if (h->h_out) cudaFreeHost(h->h_out);
   cudaGetLastError();
   delete h;
@@ -191,8 +203,10 @@ extern "C" int lb_init_random(lb_handle* h, uint64_t seed) {
 static cudaError_t step_once(lb_handle* h, int from, cudaStream_t st) {
   const void* src = h->buf[from];
   void* dst = h->buf[1 - from];
-  if (h->use_rows) return launch_step_rows(h->p.storage, src, dst, h->g, h->ph, h->d_status, st);
-  return launch_step_tile(h->p.storage, src, dst, h->g, h->ph, h->d_status, st);
+  if (h->use_rows)
+    return launch_step_rows(h->p.storage, src, dst, h->g, h->ph, h->d_body, h->d_status, h->sr,
+                            st);
+  return launch_step_tile(h->p.storage, src, dst, h->g, h->ph, h->d_status, h->sr, st);
 }
 
 static int ensure_graph(lb_handle* h, int from) {
@@ -319,6 +333,70 @@ extern "C" int lb_shear_diagnostics(lb_handle* h, double* u_k, double* i_ab) {
     return LB_ECUDA;
   if (u_k) *u_k = h->h_out[0];
   if (i_ab) *i_ab = h->h_out[1];
+  return LB_OK;
+}
+
+static void series_free(lb_handle* h) {
+  cudaFree(h->sr.buf);
+  cudaFree(h->sr.t);
+  cudaFree(h->sr.done);
+  h->sr = Series{nullptr, nullptr, nullptr, 0, 0, 0u};
+}
+
+extern "C" int lb_series_start(lb_handle* h, int64_t capacity) {
+  if (!h || capacity < 1 || capacity > (1LL << 30)) return LB_EINVAL;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LB_ECUDA;
+  drop_graphs(h);  // the captured launches carry the old record
+  series_free(h);
+  // (one spare entry: the last contribution of a step clears the next step's)
+  Series s{nullptr, nullptr, nullptr, (int)capacity + 1, h->p.k_kolmo >= 1 ? h->p.k_kolmo : 1, 0u};
+  if (cudaMalloc(&s.buf, (size_t)s.cap * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&s.t, sizeof(long long)) != cudaSuccess ||
+      cudaMalloc(&s.done, sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(s.buf);
+    cudaFree(s.t);
+    cudaFree(s.done);
+    return LB_ENOMEM;
+  }
+  if (cudaMemsetAsync(s.buf, 0, (size_t)s.cap * sizeof(double), h->stream) != cudaSuccess ||
+      cudaMemsetAsync(s.t, 0, sizeof(long long), h->stream) != cudaSuccess ||
+      cudaMemsetAsync(s.done, 0, sizeof(unsigned), h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    cudaFree(s.buf);
+    cudaFree(s.t);
+    cudaFree(s.done);
+    return LB_ECUDA;
+  }
+  h->sr = s;
+  return LB_OK;
+}
+
+extern "C" int lb_series_read(lb_handle* h, double* out, int64_t max, int64_t* count) {
+  if (!h || !h->sr.buf || max < 0 || (max > 0 && !out)) return LB_EINVAL;
+  long long t = 0;
+  if (cudaMemcpyAsync(&t, h->sr.t, sizeof(t), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return LB_ECUDA;
+  long long n = t < h->sr.cap - 1 ? t : h->sr.cap - 1;  // steps still held
+  if (n > max) n = max;
+  std::vector<double> ring((size_t)h->sr.cap);
+  if (n > 0 && (cudaMemcpyAsync(ring.data(), h->sr.buf, ring.size() * sizeof(double),
+                                cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+                cudaStreamSynchronize(h->stream) != cudaSuccess))
+    return LB_ECUDA;
+  // the most recent n steps, oldest first, as U_k = (2 / (nx ny)) sum u_x sin(k y)
+  const double scale = 2.0 / ((double)h->nx * (double)h->ny);
+  for (long long j = 0; j < n; ++j) out[j] = scale * ring[(size_t)((t - n + j) % h->sr.cap)];
+  if (count) *count = n;
+  return LB_OK;
+}
+
+extern "C" int lb_series_stop(lb_handle* h) {
+  if (!h) return LB_EINVAL;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LB_ECUDA;
+  drop_graphs(h);
+  series_free(h);
   return LB_OK;
 }
 

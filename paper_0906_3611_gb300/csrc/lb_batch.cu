@@ -31,7 +31,16 @@ struct Slot {
   PhysD ph{};
   void* buf[2] = {nullptr, nullptr};
   double* phi_w = nullptr;  // ageing snapshot phi(t_w) (lazily allocated)
+  void* body = nullptr;     // Kolmogorov body acceleration per row (nullptr: none)
 };
+
+void free_slot(Slot& s) {
+  cudaFree(s.buf[0]);
+  cudaFree(s.buf[1]);
+  cudaFree(s.phi_w);
+  cudaFree(s.body);
+  s = Slot();
+}
 
 size_t rep_bytes(int storage) {
   return storage == LB_F64 ? sizeof(ReplicaDev<double>) : sizeof(ReplicaDev<float>);
@@ -64,6 +73,7 @@ struct lb_batch {
   // handed to every launch as a PhysTable<float> or PhysTable<double>
   alignas(16) unsigned char table[sizeof(PhysTable<double>)] = {};
   int nphys = 0;
+  bool body = false;  // some replica has a Kolmogorov body-force table
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
 };
@@ -98,6 +108,8 @@ template <typename C>
 static int phys_index(lb_batch* b, const PhysD& pd) {
   Phys<C> p = make_phys<C>(pd);
   p.Uwall = C(0);  // per replica, not part of a set
+  p.gk = C(0);     // the body force is a per-replica row table
+  p.kk = C(0);
   PhysTable<C>* tab = reinterpret_cast<PhysTable<C>*>(b->table);
   for (int i = 0; i < b->nphys; ++i)
     if (memcmp(&tab->p[i], &p, sizeof(p)) == 0) return i;
@@ -114,6 +126,7 @@ static ReplicaDev<C> make_record(const Slot& s, int phys, int64_t steps) {
   r.g = s.g;
   r.phys = phys;
   r.Uwall = (C)s.ph.U;
+  r.body = s.body;
   r.buf[0] = s.buf[0];
   r.buf[1] = s.buf[1];
   r.nitems = 0;
@@ -296,6 +309,12 @@ static int rebuild_items(lb_batch* b) {
     drop_graph(b);  // the captured launches point at the old list
   }
   b->n_items = (int)items.size();
+  bool body = false;
+  for (const Slot& s : b->slots) body = body || (s.used && s.body);
+  if (body != b->body) {
+    b->body = body;
+    drop_graph(b);  // the captured launches use the other kernel variant
+  }
   if (!items.empty() &&
       cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(WorkItem),
                       cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
@@ -352,11 +371,7 @@ extern "C" void lb_batch_destroy(lb_batch* b) {
   cudaStreamSynchronize(b->stream);
   drop_graph(b);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-  for (Slot& s : b->slots) {
-    cudaFree(s.buf[0]);
-    cudaFree(s.buf[1]);
-    cudaFree(s.phi_w);
-  }
+  for (Slot& s : b->slots) free_slot(s);
   cudaFree(b->d_reps);
   cudaFree(b->d_items);
   cudaFree(b->d_offsets);
@@ -391,17 +406,16 @@ extern "C" int lb_batch_add(lb_batch* b, int nx, int ny, const lb_params* p, uin
   const int phys = b->storage == LB_F64 ? phys_index<double>(b, s.ph) : phys_index<float>(b, s.ph);
   if (phys < 0) return LB_EBUSY;  // more distinct physics sets than one launch carries
   const size_t bytes = lb_state_bytes(nx, ny, p->storage);
-  if (cudaMalloc(&s.buf[0], bytes) != cudaSuccess || cudaMalloc(&s.buf[1], bytes) != cudaSuccess) {
+  if (cudaMalloc(&s.buf[0], bytes) != cudaSuccess || cudaMalloc(&s.buf[1], bytes) != cudaSuccess ||
+      make_body_table(p->storage, s.ph, ny, &s.body, b->stream) != cudaSuccess) {
     cudaGetLastError();
-    cudaFree(s.buf[0]);
-    cudaFree(s.buf[1]);
+    free_slot(s);
     return LB_ENOMEM;
   }
   s.used = true;
   if (launch_init(p->storage, s.buf[0], g, s.ph, seed, p->init_kind, p->init, b->stream) !=
       cudaSuccess) {
-    cudaFree(s.buf[0]);
-    cudaFree(s.buf[1]);
+    free_slot(s);
     return LB_ECUDA;
   }
   const size_t rb = rep_bytes(b->storage);
@@ -416,8 +430,7 @@ extern "C" int lb_batch_add(lb_batch* b, int nx, int ny, const lb_params* p, uin
   if (cudaMemcpyAsync((char*)b->d_reps + (size_t)k * rb, rec, rb, cudaMemcpyHostToDevice,
                       b->stream) != cudaSuccess ||
       cudaStreamSynchronize(b->stream) != cudaSuccess) {
-    cudaFree(s.buf[0]);
-    cudaFree(s.buf[1]);
+    free_slot(s);
     return LB_ECUDA;
   }
   b->slots[k] = s;
@@ -433,11 +446,7 @@ extern "C" int lb_batch_remove(lb_batch* b, int slot) {
                       rep_bytes(b->storage), b->stream) != cudaSuccess ||
       cudaStreamSynchronize(b->stream) != cudaSuccess)
     return LB_ECUDA;
-  Slot& s = b->slots[slot];
-  cudaFree(s.buf[0]);
-  cudaFree(s.buf[1]);
-  cudaFree(s.phi_w);
-  s = Slot();
+  free_slot(b->slots[slot]);
   b->dirty = true;
   return LB_OK;
 }
@@ -454,7 +463,7 @@ extern "C" int lb_batch_set_steps(lb_batch* b, int slot, int64_t steps) {
 
 static cudaError_t batch_launch(lb_batch* b, cudaStream_t st) {
   return launch_step_rows_batch(b->storage, b->d_reps, b->d_items, b->d_offsets, b->grid,
-                                b->table, b->nphys, b->d_status, st);
+                                b->table, b->nphys, b->body, b->d_status, st);
 }
 
 static int ensure_batch_graph(lb_batch* b) {

@@ -50,6 +50,20 @@ inline PhysD physd_from_params(const lb_params& p) {
                            p.rho_ref, p.g_kolmo, p.k_kolmo);
 }
 
+// On-device record of the shear response after every step (Sec. VII): entry
+// t % cap accumulates sum_sites u_x sin(2 pi k y / ny) of step t (u the
+// common velocity after the step's collision); the last contributing warp
+// (or block) of a step advances *t and clears the next entry.  buf == nullptr:
+// recording off.
+struct Series {
+  double* buf;
+  long long* t;
+  unsigned* done;
+  int cap;
+  int k;
+  unsigned expected;  // contributions per step (warps of the row kernel, blocks of the tile kernel)
+};
+
 // Number of FP64 observables accumulated per block by the observe kernels:
 // {sum rho_A, sum rho_B, P_x, P_y, sum sigma_xy, wall_top, wall_bottom, 0}.
 constexpr int NOBS = 8;
@@ -58,7 +72,8 @@ size_t elem_size(int storage);
 
 // Generic fused step (tile kernel): pull-free "push" form, one launch per step.
 cudaError_t launch_step_tile(int storage, const void* src, void* dst, const Geom& g,
-                             const PhysD& ph, Status* status, cudaStream_t st);
+                             const PhysD& ph, Status* status, const Series& sr, cudaStream_t st);
+int tile_blocks(const Geom& g);
 
 // Observables of a state: per-block partial sums into `partials` (capacity
 // `cap_blocks` blocks of NOBS doubles), then a single-block finalize into out[NOBS].

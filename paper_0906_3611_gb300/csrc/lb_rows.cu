@@ -32,6 +32,11 @@
 //
 // Every mbarrier wait is bounded: on timeout the kernel sets the status word,
 // raises the CTA's abort flag, drains its own copies (bounded) and leaves.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
 #include "lb_pair.cuh"
 #include "lb_rows.h"
 #include "lb_site.cuh"
@@ -215,7 +220,7 @@ struct RowsSmem {
 // register slot (k + R) % 5, R = (iteration) % 5, so that the windows slide
 // by renaming registers instead of moving them (the window update is
 // specialised per rotation; staging and collision are shared).
-template <int STORAGE>
+template <int STORAGE, bool BODY>
 struct RowsLoop {
   using PS = PairStore<STORAGE>;
   using T2 = typename PS::T2;
@@ -235,6 +240,9 @@ struct RowsLoop {
   Status* status;
   int x0, ylo, nstage, ring;
   C Uwall;
+  const C* body;     // Kolmogorov body acceleration per row (BODY only; nullptr: none)
+  const Series& sr;  // shear-response record (sr.buf == nullptr: off)
+  C sacc;            // this thread's sum of u_x sin(k y) over its collided sites
   // this thread (a compute thread serves column x = x0 + t)
   int warp, lane, t, x, plane;
   bool active;
@@ -247,11 +255,13 @@ struct RowsLoop {
   int bad;
 
   __device__ __forceinline__ RowsLoop(const T2* __restrict__ src_, T2* __restrict__ dst,
-                                      const Geom& g_, const Phys<C>& ph_, C Uwall_, int x0_, int x1,
-                                      int ylo_, int yhi, const RowsSmem<STORAGE>& sm_, int ring_,
-                                      int* s_abort_, Status* status_)
+                                      const Geom& g_, const Phys<C>& ph_, C Uwall_,
+                                      const C* body_, int x0_, int x1, int ylo_, int yhi,
+                                      const RowsSmem<STORAGE>& sm_, int ring_, int* s_abort_,
+                                      Status* status_, const Series& sr_)
       : src(src_), g(g_), ph(ph_), sm(sm_), s_abort(s_abort_), status(status_), x0(x0_),
-        ylo(ylo_), nstage((yhi - ylo_) + 4), ring(ring_), Uwall(Uwall_) {
+        ylo(ylo_), nstage((yhi - ylo_) + 4), ring(ring_), Uwall(Uwall_), body(body_), sr(sr_),
+        sacc(C(0)) {
     warp = threadIdx.x >> 5;
     lane = threadIdx.x & 31;
     t = (warp < NCW) ? (int)threadIdx.x : 0;
@@ -412,6 +422,20 @@ struct RowsLoop {
     return v;
   }
 
+  // sin(2 pi k y / ny) of the recorded shear response (angle reduced in integers)
+  __device__ __forceinline__ C series_weight(int y) const {
+    const long long m = (2LL * sr.k * y) % (2LL * g.ny);
+    return sinpi_c<C>((C)m / (C)g.ny);
+  }
+  // one contribution per compute warp and step to the shear-response record
+  __device__ __forceinline__ void series_end(long long t0) {
+    if (!sr.buf) return;
+    double v = (double)sacc;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) series_commit(sr, t0, v);
+  }
+
   __device__ __forceinline__ bool wait_row(int j) {
     if (!mbar_wait_bounded(&sm.full[slot_of(j)], round_of(j) & 1)) {
       if (lane == 0) {
@@ -452,10 +476,14 @@ struct RowsLoop {
     if (COLLIDE) {
       // ---- row o = r - 2 (staged row q - 2) is complete: collide and push ----
       P d[9], rho;
+      C ux;
       relax(sm.stage + slot_of(q - 2) * SLOT + SOFF + t, Sx0, Sy0, Cx0, Cy0, drho0, psi0,
-            body_accel(ph, ylo + q - 4, g.ny), d, rho);
+            body_at(ylo + q - 4), d, rho, ux);
       cur = row_values(jn);
-      if (active) push(ylo + q - 4, d, rho, drho0);
+      if (active) {
+        push(ylo + q - 4, d, rho, drho0);
+        if (sr.buf) sacc += ux * series_weight(ylo + q - 4);
+      }
     } else {
       cur = row_values(jn);
     }
@@ -469,6 +497,7 @@ struct RowsLoop {
 
   // ---- a compute warp, without the pipelining (fewer live registers) ----
   __device__ __forceinline__ void consume_plain() {
+    const long long t0 = sr.buf ? *(volatile long long*)sr.t : 0;
     int R = 0;
 #pragma unroll 1
     for (int q = 0; q < nstage; ++q) {
@@ -495,9 +524,11 @@ struct RowsLoop {
         // ---- row o = r - 2 (staged row q - 2) is complete: collide and push ----
         if (q >= 4 && active) {
           P d[9], rho;
+          C ux;
           relax(sm.stage + slot_of(q - 2) * SLOT + SOFF + t, Sx0, Sy0, Cx0, Cy0, drho0, psi0,
-                body_accel(ph, ylo + q - 4, g.ny), d, rho);
+                body_at(ylo + q - 4), d, rho, ux);
           push(ylo + q - 4, d, rho, drho0);
+          if (sr.buf) sacc += ux * series_weight(ylo + q - 4);
         }
         // the warp is done with staged row q - 2
         __syncwarp();
@@ -509,6 +540,7 @@ struct RowsLoop {
     if (lane == 0) {
       for (int j = (nstage >= 2 ? nstage - 2 : 0); j < nstage; ++j) mbar_arrive(&sm.empty[slot_of(j)]);
     }
+    series_end(t0);
   }
 
   // ---- a compute warp: rows 0 .. nstage-1 ----
@@ -517,6 +549,7 @@ struct RowsLoop {
       consume_plain();
       return;
     }
+    const long long t0 = sr.buf ? *(volatile long long*)sr.t : 0;
     if (!wait_row(0)) return;
     RowVals cur = row_values(0);
     int q = 0, R = 0;
@@ -535,13 +568,20 @@ struct RowsLoop {
     if (lane == 0) {
       for (int j = (nstage >= 2 ? nstage - 2 : 0); j < nstage; ++j) mbar_arrive(&sm.empty[slot_of(j)]);
     }
+    series_end(t0);
+  }
+
+  // Kolmogorov body acceleration of row y (zero without the BODY variant)
+  __device__ __forceinline__ C body_at(int y) const {
+    if (!BODY) return C(0);
+    return body ? __ldg(body + y) : C(0);
   }
 
   // The shifted-BGK collision of one site (populations re-read from the
   // staged row): d[] becomes f*_i - w_i rho_ref (mass-exact rest population
   // for the rounded storages); rho is the site's density pair.
   __device__ __forceinline__ void relax(const T2* orow, P Sx0, P Sy0, P Cx0, P Cy0, P& drho,
-                                        P psi0, C gb, P (&d)[9], P& rho_out) {
+                                        P psi0, C gb, P (&d)[9], P& rho_out, C& ux_out) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) d[i] = PS::ld(orow[i * SW]);
     if (!RowsCfg<STORAGE>::LAG) {  // the row's drho and psi, as its staging formed them
@@ -559,6 +599,7 @@ struct RowsLoop {
     const P rw = pmul(rho, om), jxw = pmul(jx, om), jyw = pmul(jy, om);
     const C inv = div_c<C>(C(1), rw.x + rw.y);
     const C ux = (jxw.x + jxw.y) * inv, uy = (jyw.x + jyw.y) * inv;
+    ux_out = ux;
     // shifted velocity v_s = u + tau_s F_s / rho_s = u - (tau_s/rho_s) G_s
     // (branch-free: the quotient of a non-positive density is discarded)
     const bool posA = rho.x > C(0), posB = rho.y > C(0);
@@ -661,14 +702,16 @@ struct RowsLoop {
 // next staged row in the CTA's slot ring (identical in every thread); on
 // entry every slot is free or will be released by the compute warps.  A
 // bounded wait that gives up raises *s_abort (read it after a __syncthreads).
-template <int STORAGE>
+template <int STORAGE, bool BODY>
 __device__ __forceinline__ void rows_range(
     const typename PairStore<STORAGE>::T2* __restrict__ src,
     typename PairStore<STORAGE>::T2* __restrict__ dst, const Geom& g,
-    const Phys<typename Store<STORAGE>::C>& ph, typename Store<STORAGE>::C Uwall, int x0, int x1,
-    int ylo, int yhi, const RowsSmem<STORAGE>& sm, int& ring, int* s_abort, Status* status,
-    int& bad) {
-  RowsLoop<STORAGE> L(src, dst, g, ph, Uwall, x0, x1, ylo, yhi, sm, ring, s_abort, status);
+    const Phys<typename Store<STORAGE>::C>& ph, typename Store<STORAGE>::C Uwall,
+    const typename Store<STORAGE>::C* body, int x0, int x1, int ylo, int yhi,
+    const RowsSmem<STORAGE>& sm, int& ring, int* s_abort, Status* status, int& bad,
+    const Series& sr) {
+  RowsLoop<STORAGE, BODY> L(src, dst, g, ph, Uwall, body, x0, x1, ylo, yhi, sm, ring, s_abort,
+                            status, sr);
   if (L.warp == RowsCfg<STORAGE>::NCW)
     L.produce();
   else
@@ -678,11 +721,15 @@ __device__ __forceinline__ void rows_range(
 }
 
 // Single lattice: CTA b owns strip b % nstrips and row range b / nstrips.
-template <int STORAGE>
+// MODE 0: plain step; 1: with the Kolmogorov body force; 2: body force (if
+// any) and the shear-response record.  Separate variants, so that the plain
+// step carries none of their code or registers.
+template <int STORAGE, int MODE>
 __global__ void __launch_bounds__(cta_threads<STORAGE>(), RowsCfg<STORAGE>::MINB)
     k_rows(const typename PairStore<STORAGE>::T2* __restrict__ src,
            typename PairStore<STORAGE>::T2* __restrict__ dst, Geom g,
-           Phys<typename Store<STORAGE>::C> ph, int nstrips, int kranges, Status* status) {
+           Phys<typename Store<STORAGE>::C> ph, const typename Store<STORAGE>::C* body,
+           int nstrips, int kranges, Status* status, Series sr) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_abort;
   RowsSmem<STORAGE> sm(smem);
@@ -699,7 +746,9 @@ __global__ void __launch_bounds__(cta_threads<STORAGE>(), RowsCfg<STORAGE>::MINB
   }
   __syncthreads();
   int ring = 0, bad = 0;
-  rows_range<STORAGE>(src, dst, g, ph, ph.Uwall, x0, x1, ylo, yhi, sm, ring, &s_abort, status, bad);
+  const Series none = {nullptr, nullptr, nullptr, 0, 0, 0u};
+  rows_range<STORAGE, (MODE > 0)>(src, dst, g, ph, ph.Uwall, body, x0, x1, ylo, yhi, sm, ring,
+                                  &s_abort, status, bad, MODE == 2 ? sr : none);
   if (bad) atomicAdd(&status->bad_rho, (unsigned)bad);
 }
 
@@ -711,7 +760,8 @@ __global__ void __launch_bounds__(cta_threads<STORAGE>(), RowsCfg<STORAGE>::MINB
 // budget; replicas with no budget left are skipped.
 // ONE: every replica uses physics set 0 (the constants are then addressed
 // like the single-lattice kernel's parameters, without an index computation).
-template <int STORAGE, bool ONE>
+// BODY: some replica has a Kolmogorov body force.
+template <int STORAGE, bool ONE, bool BODY>
 __global__ void __launch_bounds__(cta_threads<STORAGE>(), RowsCfg<STORAGE>::MINB)
     k_rows_batch(ReplicaDev<typename Store<STORAGE>::C>* __restrict__ reps,
                  const WorkItem* __restrict__ items, const int* __restrict__ offsets,
@@ -723,6 +773,7 @@ __global__ void __launch_bounds__(cta_threads<STORAGE>(), RowsCfg<STORAGE>::MINB
   __shared__ int s_skip;
   __shared__ int s_phys;
   __shared__ C s_U;
+  __shared__ const C* s_body;
   __shared__ WorkItem s_item;
   __shared__ Geom s_g;
   __shared__ const T2* s_src;
@@ -743,13 +794,16 @@ __global__ void __launch_bounds__(cta_threads<STORAGE>(), RowsCfg<STORAGE>::MINB
       s_g = R.g;
       s_phys = R.phys;
       s_U = R.Uwall;
+      s_body = (const C*)R.body;
       s_src = (const T2*)R.buf[R.parity];
       s_dst = (T2*)R.buf[1 - R.parity];
     }
     __syncthreads();
     if (s_skip) continue;
-    rows_range<STORAGE>(s_src, s_dst, s_g, tab.p[ONE ? 0 : s_phys], s_U, s_item.x0, s_item.x1,
-                        s_item.ylo, s_item.yhi, sm, ring, &s_abort, status, bad);
+    const Series none = {nullptr, nullptr, nullptr, 0, 0, 0u};  // (no record in batches)
+    rows_range<STORAGE, BODY>(s_src, s_dst, s_g, tab.p[ONE ? 0 : s_phys], s_U, s_body, s_item.x0,
+                              s_item.x1, s_item.ylo, s_item.yhi, sm, ring, &s_abort, status, bad,
+                              none);
     __syncthreads();
     if (s_abort) break;
     if (threadIdx.x == 0) {
@@ -768,30 +822,35 @@ __global__ void __launch_bounds__(cta_threads<STORAGE>(), RowsCfg<STORAGE>::MINB
 
 // ---- launchers ----
 
+// Resident CTAs per SM of a kernel variant at the row kernels' shared memory.
+template <typename K>
+static int per_sm_of(K kernel, int threads, size_t smem) {
+  int n = 0;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem);
+  return n;
+}
+
 template <int STORAGE, bool BATCH>
 static int resident_blocks() {
   static int cached = -1;
   if (cached < 0) {
     const size_t smem = rows_smem_bytes<STORAGE>();
+    const int th = cta_threads<STORAGE>();
     int per_sm = 0, dev = 0, sms = 0;
     if (BATCH) {
-      cudaFuncSetAttribute(k_rows_batch<STORAGE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
-      cudaFuncSetAttribute(k_rows_batch<STORAGE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
-      int per_sm1 = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows_batch<STORAGE, false>,
-                                                    cta_threads<STORAGE>(), smem);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, k_rows_batch<STORAGE, true>,
-                                                    cta_threads<STORAGE>(), smem);
-      if (per_sm1 < per_sm) per_sm = per_sm1;
+      const int n[4] = {per_sm_of(k_rows_batch<STORAGE, false, false>, th, smem),
+                        per_sm_of(k_rows_batch<STORAGE, false, true>, th, smem),
+                        per_sm_of(k_rows_batch<STORAGE, true, false>, th, smem),
+                        per_sm_of(k_rows_batch<STORAGE, true, true>, th, smem)};
+      per_sm = std::min(std::min(n[0], n[1]), std::min(n[2], n[3]));
     } else {
-      cudaFuncSetAttribute(k_rows<STORAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows<STORAGE>, cta_threads<STORAGE>(),
-                                                    smem);
+      const int n[3] = {per_sm_of(k_rows<STORAGE, 0>, th, smem),
+                        per_sm_of(k_rows<STORAGE, 1>, th, smem),
+                        per_sm_of(k_rows<STORAGE, 2>, th, smem)};
+      per_sm = std::min(n[0], std::min(n[1], n[2]));
     }
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, (cudaGetDevice(&dev), dev));
     cached = per_sm * sms;
   }
   return cached;
@@ -836,52 +895,103 @@ bool rows_supported(const Geom& g, int storage) {
 
 int rows_batch_grid(int storage) { return resident(storage, true); }
 
+cudaError_t make_body_table(int storage, const PhysD& ph, int ny, void** out, cudaStream_t st) {
+  *out = nullptr;
+  if (ph.gk == 0.0) return cudaSuccess;
+  // the same expression as the oracle's force pass, then rounded to the arithmetic type
+  std::vector<double> v((size_t)ny);
+  for (int y = 0; y < ny; ++y) v[y] = ph.gk * sin(2.0 * M_PI * (double)ph.kk * (double)y / (double)ny);
+  std::vector<float> vf;
+  const void* host = v.data();
+  size_t bytes = (size_t)ny * sizeof(double);
+  if (storage != LB_F64) {
+    vf.assign(v.begin(), v.end());
+    host = vf.data();
+    bytes = (size_t)ny * sizeof(float);
+  }
+  cudaError_t e = cudaMalloc(out, bytes);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(*out, host, bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaFree(*out);
+    *out = nullptr;
+  }
+  return e;
+}
+
 template <int STORAGE>
 static cudaError_t rows_t(const void* src, void* dst, const Geom& g, const PhysD& pd,
-                          Status* status, cudaStream_t st) {
+                          const void* body_v, Status* status, const Series& sr_in,
+                          cudaStream_t st) {
+  using C = typename Store<STORAGE>::C;
+  const C* body = (const C*)body_v;
   using T2 = typename PairStore<STORAGE>::T2;
   const int nstrips = rows_nstrips(g.nx, strip_cols<STORAGE>());
   int k = resident(STORAGE, false) / nstrips;
   if (k < 1) k = 1;
   if (k > g.ny) k = g.ny;
   const size_t smem = rows_smem_bytes<STORAGE>();
-  k_rows<STORAGE><<<nstrips * k, cta_threads<STORAGE>(), smem, st>>>(
-      (const T2*)src, (T2*)dst, g, make_phys<typename Store<STORAGE>::C>(pd), nstrips, k, status);
+  Series sr = sr_in;
+  sr.expected = (unsigned)(nstrips * k * RowsCfg<STORAGE>::NCW);  // every compute warp, once
+  const Phys<C> ph = make_phys<C>(pd);
+  const int nb = nstrips * k, th = cta_threads<STORAGE>();
+  if (sr.buf)
+    k_rows<STORAGE, 2><<<nb, th, smem, st>>>((const T2*)src, (T2*)dst, g, ph, body, nstrips, k,
+                                            status, sr);
+  else if (body)
+    k_rows<STORAGE, 1><<<nb, th, smem, st>>>((const T2*)src, (T2*)dst, g, ph, body, nstrips, k,
+                                            status, sr);
+  else
+    k_rows<STORAGE, 0><<<nb, th, smem, st>>>((const T2*)src, (T2*)dst, g, ph, body, nstrips, k,
+                                            status, sr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_step_rows(int storage, const void* src, void* dst, const Geom& g,
-                             const PhysD& ph, Status* status, cudaStream_t st) {
+                             const PhysD& ph, const void* body, Status* status, const Series& sr,
+                             cudaStream_t st) {
   switch (storage) {
-    case LB_F64: return rows_t<LB_F64>(src, dst, g, ph, status, st);
-    case LB_F32: return rows_t<LB_F32>(src, dst, g, ph, status, st);
-    case LB_BF16_DEV: return rows_t<LB_BF16_DEV>(src, dst, g, ph, status, st);
-    case LB_F16_DEV: return rows_t<LB_F16_DEV>(src, dst, g, ph, status, st);
+    case LB_F64: return rows_t<LB_F64>(src, dst, g, ph, body, status, sr, st);
+    case LB_F32: return rows_t<LB_F32>(src, dst, g, ph, body, status, sr, st);
+    case LB_BF16_DEV: return rows_t<LB_BF16_DEV>(src, dst, g, ph, body, status, sr, st);
+    case LB_F16_DEV: return rows_t<LB_F16_DEV>(src, dst, g, ph, body, status, sr, st);
   }
   return cudaErrorInvalidValue;
 }
 
 template <int STORAGE>
 static cudaError_t rows_batch_t(void* reps, const WorkItem* items, const int* offsets, int grid,
-                                const void* table, int nphys, Status* status, cudaStream_t st) {
+                                const void* table, int nphys, bool body, Status* status,
+                                cudaStream_t st) {
   using C = typename Store<STORAGE>::C;
-  if (nphys <= 1)
-    k_rows_batch<STORAGE, true><<<grid, cta_threads<STORAGE>(), rows_smem_bytes<STORAGE>(), st>>>(
-        (ReplicaDev<C>*)reps, items, offsets, status, *(const PhysTable<C>*)table);
+  auto* R = (ReplicaDev<C>*)reps;
+  const PhysTable<C>& tab = *(const PhysTable<C>*)table;
+  const int th = cta_threads<STORAGE>();
+  const size_t smem = rows_smem_bytes<STORAGE>();
+  if (nphys <= 1 && !body)
+    k_rows_batch<STORAGE, true, false><<<grid, th, smem, st>>>(R, items, offsets, status, tab);
+  else if (nphys <= 1)
+    k_rows_batch<STORAGE, true, true><<<grid, th, smem, st>>>(R, items, offsets, status, tab);
+  else if (!body)
+    k_rows_batch<STORAGE, false, false><<<grid, th, smem, st>>>(R, items, offsets, status, tab);
   else
-    k_rows_batch<STORAGE, false><<<grid, cta_threads<STORAGE>(), rows_smem_bytes<STORAGE>(), st>>>(
-        (ReplicaDev<C>*)reps, items, offsets, status, *(const PhysTable<C>*)table);
+    k_rows_batch<STORAGE, false, true><<<grid, th, smem, st>>>(R, items, offsets, status, tab);
   return cudaGetLastError();
 }
 
 cudaError_t launch_step_rows_batch(int storage, void* reps, const WorkItem* items,
                                    const int* offsets, int grid, const void* table, int nphys,
-                                   Status* status, cudaStream_t st) {
+                                   bool body, Status* status, cudaStream_t st) {
   switch (storage) {
-    case LB_F64: return rows_batch_t<LB_F64>(reps, items, offsets, grid, table, nphys, status, st);
-    case LB_F32: return rows_batch_t<LB_F32>(reps, items, offsets, grid, table, nphys, status, st);
-    case LB_BF16_DEV: return rows_batch_t<LB_BF16_DEV>(reps, items, offsets, grid, table, nphys, status, st);
-    case LB_F16_DEV: return rows_batch_t<LB_F16_DEV>(reps, items, offsets, grid, table, nphys, status, st);
+    case LB_F64:
+      return rows_batch_t<LB_F64>(reps, items, offsets, grid, table, nphys, body, status, st);
+    case LB_F32:
+      return rows_batch_t<LB_F32>(reps, items, offsets, grid, table, nphys, body, status, st);
+    case LB_BF16_DEV:
+      return rows_batch_t<LB_BF16_DEV>(reps, items, offsets, grid, table, nphys, body, status, st);
+    case LB_F16_DEV:
+      return rows_batch_t<LB_F16_DEV>(reps, items, offsets, grid, table, nphys, body, status, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -20,6 +20,7 @@ struct ReplicaDev {
   Geom g;
   int phys;            // index into the launch's PhysTable
   C Uwall;             // Couette wall speed of this replica
+  const void* body;    // Kolmogorov body acceleration per row (C[ny]; nullptr: none)
   void* buf[2];        // the two population buffers
   int nitems;          // work items of this replica per step
   int parity;          // buffer holding the current state
@@ -52,17 +53,24 @@ bool rows_supported(const Geom& g, int storage);
 // Persistent grid size (resident CTAs) of the batched kernel.
 int rows_batch_grid(int storage);
 
+// `body`: the Kolmogorov body acceleration of every row, ny values of the
+// storage's arithmetic type (float, or double for FP64), or nullptr.
 cudaError_t launch_step_rows(int storage, const void* src, void* dst, const Geom& g,
-                             const PhysD& ph, Status* status, cudaStream_t st);
+                             const PhysD& ph, const void* body, Status* status, const Series& sr,
+                             cudaStream_t st);
+
+// Device table of the Kolmogorov body acceleration g sin(2 pi k y / ny), y in
+// [0, ny), in the arithmetic type of `storage` (cudaMalloc'd; nullptr when g = 0).
+cudaError_t make_body_table(int storage, const PhysD& ph, int ny, void** out, cudaStream_t st);
 
 // One step of every replica with budget left; `reps` is a device array of
 // ReplicaDev<float> (FP32 and 16-bit storages) or ReplicaDev<double> (FP64).
 // CTA c of the persistent grid works on items [offsets[c], offsets[c+1]);
 // `table` is a host PhysTable<float> (FP32 and 16-bit storages) or
 // PhysTable<double> (FP64) with `nphys` sets in use, copied into the launch's
-// parameters.
+// parameters; `body`: some replica has a body-force table.
 cudaError_t launch_step_rows_batch(int storage, void* reps, const WorkItem* items,
                                    const int* offsets, int grid, const void* table, int nphys,
-                                   Status* status, cudaStream_t st);
+                                   bool body, Status* status, cudaStream_t st);
 
 }  // namespace lbk

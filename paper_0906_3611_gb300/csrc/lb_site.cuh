@@ -3,6 +3,7 @@
 #pragma once
 
 #include "lb_common.cuh"
+#include "lb_kernels.h"
 
 namespace lbk {
 
@@ -106,6 +107,20 @@ __device__ __forceinline__ void bgk_fast(const Phys<C>& ph, C (&d)[2][9], const 
 template <typename C>
 __device__ __forceinline__ C wall_term(int i, C rho_s, C Uw) {
   return C(6) * wq<C>(i) * rho_s * C(Q9::cx(i)) * Uw;
+}
+
+// Adds one contribution to the series entry of the current step and, for the
+// last contribution of the step, advances the step count and clears the next
+// entry.  Called by one thread per contributing warp (or block).
+__device__ __forceinline__ void series_commit(const Series& sr, long long t, double v) {
+  atomicAdd(&sr.buf[t % sr.cap], v);
+  __threadfence();
+  if (atomicAdd(sr.done, 1u) == sr.expected - 1) {
+    sr.buf[(t + 1) % sr.cap] = 0.0;
+    *sr.t = t + 1;
+    *sr.done = 0u;
+    __threadfence();
+  }
 }
 
 }  // namespace lbk

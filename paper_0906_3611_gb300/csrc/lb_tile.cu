@@ -35,7 +35,8 @@ template <int STORAGE, bool OBSERVE>
 __global__ void __launch_bounds__(TTHREADS)
     k_tile(const typename Store<STORAGE>::T* __restrict__ src,
            typename Store<STORAGE>::T* __restrict__ dst, Geom g,
-           Phys<typename Store<STORAGE>::C> ph, Status* status, double* __restrict__ partials) {
+           Phys<typename Store<STORAGE>::C> ph, Status* status, double* __restrict__ partials,
+           Series sr) {
   using S = Store<STORAGE>;
   using T = typename S::T;
   using C = typename S::C;
@@ -68,6 +69,7 @@ __global__ void __launch_bounds__(TTHREADS)
 #pragma unroll
   for (int k = 0; k < NOBS; ++k) acc[k] = 0.0;
   int bad = 0;
+  double sval = 0.0;  // this site's shear-response term (recording on)
 
   if (active) {
     C d[2][9];
@@ -116,6 +118,12 @@ __global__ void __launch_bounds__(TTHREADS)
     momenta<C>(d, jx, jy);
     C vx[2], vy[2];
     shifted_velocities<C>(ph, rho, jx, jy, Fx, Fy, vx, vy, bad);
+    if (!OBSERVE && sr.buf) {  // shear response: u_x sin(2 pi k y / ny) of this site
+      const C den = rho[0] * ph.omega[0] + rho[1] * ph.omega[1];
+      const long long m = (2LL * sr.k * y) % (2LL * g.ny);
+      sval = (double)(div_c<C>(jx[0] * ph.omega[0] + jx[1] * ph.omega[1], den) *
+                      sinpi_c<C>((C)m / (C)g.ny));
+    }
 
     if (OBSERVE) {
       // densities in FP64 from the reference and the summed deviation (the
@@ -200,6 +208,19 @@ __global__ void __launch_bounds__(TTHREADS)
     }
   }
   if (bad) atomicAdd(&status->bad_rho, (unsigned)bad);
+
+  if (!OBSERVE && sr.buf) {  // one contribution per block and step
+    __shared__ double sred[TTHREADS];
+    __shared__ long long s_t;
+    if (tid == 0) s_t = *(volatile long long*)sr.t;
+    sred[tid] = sval;
+    __syncthreads();
+    for (int stride = TTHREADS / 2; stride > 0; stride >>= 1) {
+      if (tid < stride) sred[tid] += sred[tid + stride];
+      __syncthreads();
+    }
+    if (tid == 0) series_commit(sr, s_t, sred[0]);
+  }
 
   if (OBSERVE) {
     // deterministic tree reduction of the block's sums
@@ -420,21 +441,25 @@ int observe_blocks(const Geom& g) {
 
 template <int STORAGE>
 static cudaError_t step_tile_t(const void* src, void* dst, const Geom& g, const PhysD& pd,
-                               Status* status, cudaStream_t st) {
+                               Status* status, const Series& sr_in, cudaStream_t st) {
   using S = Store<STORAGE>;
+  Series sr = sr_in;
+  sr.expected = (unsigned)tile_blocks(g);  // every block, once
   k_tile<STORAGE, false><<<tile_grid(g), TTHREADS, 0, st>>>(
       (const typename S::T*)src, (typename S::T*)dst, g, make_phys<typename S::C>(pd), status,
-      nullptr);
+      nullptr, sr);
   return cudaGetLastError();
 }
 
+int tile_blocks(const Geom& g) { return observe_blocks(g); }
+
 cudaError_t launch_step_tile(int storage, const void* src, void* dst, const Geom& g,
-                             const PhysD& ph, Status* status, cudaStream_t st) {
+                             const PhysD& ph, Status* status, const Series& sr, cudaStream_t st) {
   switch (storage) {
-    case LB_F64: return step_tile_t<LB_F64>(src, dst, g, ph, status, st);
-    case LB_F32: return step_tile_t<LB_F32>(src, dst, g, ph, status, st);
-    case LB_BF16_DEV: return step_tile_t<LB_BF16_DEV>(src, dst, g, ph, status, st);
-    case LB_F16_DEV: return step_tile_t<LB_F16_DEV>(src, dst, g, ph, status, st);
+    case LB_F64: return step_tile_t<LB_F64>(src, dst, g, ph, status, sr, st);
+    case LB_F32: return step_tile_t<LB_F32>(src, dst, g, ph, status, sr, st);
+    case LB_BF16_DEV: return step_tile_t<LB_BF16_DEV>(src, dst, g, ph, status, sr, st);
+    case LB_F16_DEV: return step_tile_t<LB_F16_DEV>(src, dst, g, ph, status, sr, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -443,8 +468,9 @@ template <int STORAGE>
 static cudaError_t observe_t(const void* src, const Geom& g, const PhysD& pd, Status* status,
                              double* partials, cudaStream_t st) {
   using S = Store<STORAGE>;
+  const Series none = {nullptr, nullptr, nullptr, 0, 0, 0u};
   k_tile<STORAGE, true><<<tile_grid(g), TTHREADS, 0, st>>>(
-      (const typename S::T*)src, nullptr, g, make_phys<typename S::C>(pd), status, partials);
+      (const typename S::T*)src, nullptr, g, make_phys<typename S::C>(pd), status, partials, none);
   return cudaGetLastError();
 }
 

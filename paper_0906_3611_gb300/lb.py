@@ -24,7 +24,8 @@ ELEM_BYTES = {LB_F64: 8, LB_F32: 4, LB_BF16_DEV: 2, LB_F16_DEV: 2}
 
 # every entry point declared in include/lb.h
 EXPORTED = ["lb_state_bytes", "lb_create", "lb_create_on", "lb_init_random", "lb_step",
-            "lb_observables", "lb_shear_diagnostics", "lb_phi_snapshot", "lb_phi_overlap",
+            "lb_observables", "lb_shear_diagnostics", "lb_series_start", "lb_series_read",
+            "lb_series_stop", "lb_phi_snapshot", "lb_phi_overlap",
             "lb_get_state", "lb_set_state",
             "lb_set_state_raw",
             "lb_get_state_raw", "lb_time", "lb_status", "lb_sync", "lb_destroy", "lb_strerror",
@@ -67,6 +68,9 @@ def _load():
         "lb_step": (ctypes.c_int, [vp, ctypes.c_int64]),
         "lb_observables": (ctypes.c_int, [vp, dp, dp, dp, dp]),
         "lb_shear_diagnostics": (ctypes.c_int, [vp, dp, dp]),
+        "lb_series_start": (ctypes.c_int, [vp, ctypes.c_int64]),
+        "lb_series_read": (ctypes.c_int, [vp, dp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+        "lb_series_stop": (ctypes.c_int, [vp]),
         "lb_phi_snapshot": (ctypes.c_int, [vp]),
         "lb_phi_overlap": (ctypes.c_int, [vp, dp, dp]),
         "lb_batch_phi_snapshot": (ctypes.c_int, [vp, ctypes.c_int]),
@@ -181,6 +185,21 @@ def lb_shear_diagnostics(h: int) -> tuple[float, float]:
     iab = np.zeros(1)
     _check(_lib.lb_shear_diagnostics(h, _dp(uk), _dp(iab)), "lb_shear_diagnostics")
     return float(uk[0]), float(iab[0])
+
+
+def lb_series_start(h: int, capacity: int) -> None:
+    _check(_lib.lb_series_start(h, capacity), "lb_series_start")
+
+
+def lb_series_read(h: int, max_count: int) -> np.ndarray:
+    out = np.zeros(max(max_count, 1))
+    n = ctypes.c_int64(0)
+    _check(_lib.lb_series_read(h, _dp(out), max_count, ctypes.byref(n)), "lb_series_read")
+    return out[:n.value].copy()
+
+
+def lb_series_stop(h: int) -> None:
+    _check(_lib.lb_series_stop(h), "lb_series_stop")
 
 
 def lb_phi_snapshot(h: int) -> None:
@@ -349,6 +368,19 @@ class Lattice:
 
     def step(self, n: int = 1):
         lb_step(self.h, n)
+        return self
+
+    def series_start(self, capacity: int):
+        """Record U_k after every step (device ring of `capacity` entries)."""
+        lb_series_start(self.h, capacity)
+        return self
+
+    def series(self, max_count: int = 1 << 20) -> np.ndarray:
+        """The recorded U_k, oldest first (R = U_k / U0)."""
+        return lb_series_read(self.h, max_count)
+
+    def series_stop(self):
+        lb_series_stop(self.h)
         return self
 
     def phi_snapshot(self):

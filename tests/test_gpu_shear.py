@@ -156,3 +156,56 @@ def test_batched_overlap_equals_the_lattice_alone(lb, monkeypatch):
     lat = lb.Lattice(128, 128, p).init_random(5).step(30).phi_snapshot().step(30)
     assert lat.phi_overlap() == got
     lat.close()
+
+
+@pytest.mark.parametrize("kernel", ["rows", "tile"])
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_series_records_the_response_of_every_step(lb, monkeypatch, kernel, storage, tol):
+    """Entry t of the record is U_k of the state at the start of step t."""
+    st = {"f64": lb.LB_F64, "f32": lb.LB_F32}[storage]
+    monkeypatch.setenv("LB_STEP_KERNEL", kernel)
+    p = lb.make_params(**STD07, storage=st, rho_ref=(0.612, 0.612),
+                       init_kind=lb.LB_INIT_UNIFORM_NOISE, init=(0.612, 0.612, 0.01),
+                       g_kolmo=5e-5, k_kolmo=2)
+    lat = lb.Lattice(256, 96, p).init_random(3).step(10)
+    lat.series_start(16)
+    expect = []
+    for _ in range(40):  # diagnostics of each state, then the step that records it
+        expect.append(lat.shear_diagnostics()["U_k"])
+        lat.step(1)
+    got = lat.series()
+    assert lat.status() == lb.LB_OK
+    assert len(got) == 16  # the ring keeps the most recent 16 steps
+    assert np.max(np.abs(got - np.array(expect[-16:]))) <= tol * np.max(np.abs(expect))
+    lat.step(64)  # graph-replayed steps record too
+    assert len(lat.series()) == 16
+    lat.series_stop().step(3)
+    with pytest.raises(lb.LBError):
+        lat.series()
+    lat.close()
+
+
+def test_batch_with_forced_and_plain_replicas_coming_and_going(lb, monkeypatch):
+    """Forced and unforced replicas share a launch; removing the forced one
+    switches the batch back to the plain kernel variant mid-run."""
+    common = dict(STD07, storage=lb.LB_F32, rho_ref=(0.612, 0.612),
+                  init_kind=lb.LB_INIT_UNIFORM_NOISE, init=(0.612, 0.612, 0.01))
+    pf = lb.make_params(**common, g_kolmo=4e-5, k_kolmo=1)
+    pp = lb.make_params(**common)
+    b = lb.Batch(4, lb.LB_F32)
+    sf = b.add(128, 128, pf, 1, 64)
+    sp = b.add(160, 64, pp, 2, 64)
+    b.run(32)  # two replayed 16-step graphs
+    forced = b.get_state(sf)
+    b.remove(sf)
+    b.run(32)
+    assert b.status() == lb.LB_OK
+    plain = b.get_state(sp)
+    b.close()
+    monkeypatch.setenv("LB_STEP_KERNEL", "rows")
+    lat = lb.Lattice(128, 128, pf).init_random(1).step(32)
+    assert np.array_equal(lat.get_state(), forced)
+    lat.close()
+    lat = lb.Lattice(160, 64, pp).init_random(2).step(64)
+    assert np.array_equal(lat.get_state(), plain)
+    lat.close()
