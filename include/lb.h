@@ -290,6 +290,11 @@ LB_API int lb_batch_poll(lb_batch *b, int64_t *remaining, int64_t *steps_done);
 LB_API int lb_batch_observables(lb_batch *b, int slot, double *rho, double *u, double *stress,
                                 double *mass);
 LB_API int lb_batch_get_state(lb_batch *b, int slot, double *f);
+
+/* lb_set_state of one replica: replaces its current state with the FP64
+ * populations f (layout of lb_get_state; converted to the batch's storage),
+ * keeping its step budget and step count.  Synchronises. */
+LB_API int lb_batch_set_state(lb_batch *b, int slot, const double *f);
 /* lb_shear_diagnostics, lb_phi_snapshot and lb_phi_overlap of one replica
  * (synchronise; a replica's snapshot is freed with the replica). */
 LB_API int lb_batch_shear_diagnostics(lb_batch *b, int slot, double *u_k, double *i_ab);

@@ -186,3 +186,14 @@ def sigma_flat_profile(rhoA: np.ndarray, rhoB: np.ndarray, tau: float, G_AB: flo
     if window is not None:
         integrand = integrand[window]
     return float(CS2 ** 2 * integrand.sum())
+
+
+def zero_crossing(xs, ys) -> float:
+    """x at which the sampled function y(x) first changes sign, by linear
+    interpolation between the two bracketing samples (xs increasing)."""
+    for k in range(len(xs) - 1):
+        if ys[k] == 0.0:
+            return float(xs[k])
+        if ys[k] * ys[k + 1] < 0.0:
+            return float(xs[k] - ys[k] * (xs[k + 1] - xs[k]) / (ys[k + 1] - ys[k]))
+    raise ValueError("no sign change in the samples")

@@ -736,6 +736,24 @@ extern "C" int lb_batch_get_state(lb_batch* b, int slot, double* f) {
   return cudaStreamSynchronize(b->stream) == cudaSuccess ? LB_OK : LB_ECUDA;
 }
 
+extern "C" int lb_batch_set_state(lb_batch* b, int slot, const double* f) {
+  if (!b || !f || slot < 0 || slot >= b->capacity || !b->slots[slot].used) return LB_EINVAL;
+  const Slot& s = b->slots[slot];
+  void* cur = nullptr;
+  int rc = current_buffer(b, slot, &cur);  // (synchronises: no step is in flight)
+  if (rc) return rc;
+  const size_t n = (size_t)s.nx * s.ny;
+  rc = ensure_stage_b(b, n * sizeof(double));
+  if (rc) return rc;
+  for (int q = 0; q < 18; ++q) {
+    if (cudaMemcpyAsync(b->d_stage, f + (size_t)q * n, n * sizeof(double), cudaMemcpyHostToDevice,
+                        b->stream) != cudaSuccess ||
+        launch_pack_plane(s.p.storage, b->d_stage, cur, s.g, s.ph, q, b->stream) != cudaSuccess)
+      return LB_ECUDA;
+  }
+  return cudaStreamSynchronize(b->stream) == cudaSuccess ? LB_OK : LB_ECUDA;
+}
+
 extern "C" int lb_batch_autotune(lb_batch* b, int steps_per_candidate, int* layout,
                                  int* rows_per_item) {
   if (!b || steps_per_candidate < 1) return LB_EINVAL;

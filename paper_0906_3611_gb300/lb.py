@@ -31,7 +31,7 @@ EXPORTED = ["lb_state_bytes", "lb_create", "lb_create_on", "lb_init_random", "lb
             "lb_get_state_raw", "lb_time", "lb_status", "lb_sync", "lb_destroy", "lb_strerror",
             "lb_observables_noalloc", "lb_batch_create", "lb_batch_add", "lb_batch_remove",
             "lb_batch_set_steps", "lb_batch_run", "lb_batch_poll", "lb_batch_observables",
-            "lb_batch_get_state", "lb_batch_shear_diagnostics", "lb_batch_phi_snapshot",
+            "lb_batch_get_state", "lb_batch_set_state", "lb_batch_shear_diagnostics", "lb_batch_phi_snapshot",
             "lb_batch_phi_overlap", "lb_batch_autotune",
             "lb_batch_status", "lb_batch_destroy"]
 
@@ -95,6 +95,7 @@ def _load():
         "lb_batch_poll": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
         "lb_batch_observables": (ctypes.c_int, [vp, ctypes.c_int, dp, dp, dp, dp]),
         "lb_batch_get_state": (ctypes.c_int, [vp, ctypes.c_int, dp]),
+        "lb_batch_set_state": (ctypes.c_int, [vp, ctypes.c_int, dp]),
         "lb_batch_shear_diagnostics": (ctypes.c_int, [vp, ctypes.c_int, dp, dp]),
         "lb_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                              ctypes.POINTER(ctypes.c_int)]),
@@ -309,6 +310,11 @@ def lb_batch_get_state(b: int, slot: int, f: np.ndarray) -> None:
     _check(_lib.lb_batch_get_state(b, slot, _dp(f)), "lb_batch_get_state")
 
 
+def lb_batch_set_state(b: int, slot: int, f: np.ndarray) -> None:
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    _check(_lib.lb_batch_set_state(b, slot, _dp(f)), "lb_batch_set_state")
+
+
 def lb_batch_shear_diagnostics(b: int, slot: int) -> tuple[float, float]:
     uk = np.zeros(1)
     iab = np.zeros(1)
@@ -491,6 +497,15 @@ class Batch:
         f = np.empty((2, 9, ny, nx))
         lb_batch_get_state(self.h, slot, f)
         return f
+
+    def set_state(self, slot: int, f: np.ndarray):
+        """Replace the replica's state by FP64 populations [2][9][ny][nx]."""
+        nx, ny = self.shapes[slot]
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        if f.shape != (2, 9, ny, nx):
+            raise ValueError(f"state of shape {f.shape}, expected {(2, 9, ny, nx)}")
+        lb_batch_set_state(self.h, slot, f)
+        return self
 
     def shear_diagnostics(self, slot: int) -> dict:
         uk, iab = lb_batch_shear_diagnostics(self.h, slot)

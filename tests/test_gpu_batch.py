@@ -120,3 +120,35 @@ def test_autotune_keeps_results_exact(lb, monkeypatch):
     ref = _alone(lb, monkeypatch, 512, 256, _p(lb, CFG, lb.LB_F32, 1, 0.02), 7, n)
     assert np.array_equal(got, ref)
     assert obs["mass"][0] > 0
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_set_state_of_a_replica_mid_run(lb, monkeypatch, storage):
+    """lb_batch_set_state replaces one replica's state after some steps; the
+    replica then continues exactly like a lattice started from that state
+    (FP64: the state reads back bit for bit), and its neighbour is untouched."""
+    st = {"f64": lb.LB_F64, "f32": lb.LB_F32}[storage]
+    import inputs
+    w9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    nx, ny = 128, 40
+    f = inputs.populations(nx, ny, seed=31, base=w9, rel_amp=0.05, species_scale=(0.9, 0.45))
+    if storage == "f32":
+        f = f.astype(np.float32).astype(np.float64)
+    p = _p(lb, CFG, st, 1, 0.02)
+    q = _p(lb, ASYM, st, 0, 0.0)
+    b = lb.Batch(2, st)
+    k = b.add(nx, ny, p, 1, 25)
+    k2 = b.add(64, 24, q, 2, 25)
+    b.run(5)
+    b.set_state(k, f)
+    if storage == "f64":
+        assert np.array_equal(b.get_state(k), f)
+    b.run(20)
+    got, other = b.get_state(k), b.get_state(k2)
+    assert b.status() == lb.LB_OK
+    b.close()
+    monkeypatch.setenv("LB_STEP_KERNEL", "rows")
+    lat = lb.Lattice(nx, ny, p).set_state(f).step(20)
+    assert np.array_equal(lat.get_state(), got)
+    lat.close()
+    assert np.array_equal(_alone(lb, monkeypatch, 64, 24, q, 2, 25), other)
