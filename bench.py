@@ -461,6 +461,8 @@ def run_shear(args):
     stream.synchronize()
     for r in range(n):  # the ageing snapshot phi(t_w) at t_w = warmup
         b.phi_snapshot(r)
+    for r in range(n):  # U_k of every timed step, recorded on the device
+        b.series_start(r, args.steps)
     D.barrier()
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
@@ -474,7 +476,14 @@ def run_shear(args):
     status = b.status()
     diag = [b.shear_diagnostics(r) for r in range(n)]
     ov = [b.phi_overlap(r) for r in range(n)]
+    series = np.array([b.series(r) for r in range(n)]) / U0  # R(t) per replica
+    nb = 24
+    bursts = [b.series_bursts(r, 3.0, nb) for r in range(n)]
     b.close()
+    # ensemble kurtosis K(t) = <R^4>/<R^2>^2 over the replicas at each recorded step (Fig. 16)
+    Kt = np.mean(series ** 4, axis=0) / np.mean(series ** 2, axis=0) ** 2
+    hist = np.sum([x["hist"] for x in bursts], axis=0)
+    events = int(sum(x["events"] for x in bursts))
     C = D.sum(sum(o[0] for o in ov)) / D.sum(sum(o[1] for o in ov))
     R = np.array(D.gather([d["U_k"] / U0 for d in diag]))
     iab = np.array(D.gather([d["I_AB"] for d in diag]))
@@ -492,6 +501,7 @@ def run_shear(args):
                 "config": {"workload": args.workload, "replicas": n, "side": side,
                            "couplings": "rho0 = 0.7 standard set", "U0": U0, "g_kolmo": g,
                            "storage": STORAGE_NAME[storage],
+                           "record": "U_k of every timed step, per replica, on the device",
                            "work_list": {"layout": ["contiguous", "packed"][layout],
                                          "max_piece_rows": rows},
                            "l2": f"{sites * 18 * es / 1e6:.0f} MB read per step: partly "
@@ -502,7 +512,12 @@ def run_shear(args):
                 "response": {"t": args.warmup + args.steps, "R_mean": float(R.mean()),
                              "R_kurtosis": float(np.mean(R ** 4) / np.mean(R ** 2) ** 2),
                              "I_AB_mean": float(iab.mean()),
-                             "overlap_C": {"t_w": args.warmup, "dt_w": args.steps, "C": C}},
+                             "overlap_C": {"t_w": args.warmup, "dt_w": args.steps, "C": C},
+                             "kurtosis_t": {"recorded_steps": int(Kt.size),
+                                            "final": float(Kt[-1]), "mean": float(Kt.mean()),
+                                            "max": float(Kt.max())},
+                             "bursts": {"c_sigma": 3.0, "events": events,
+                                        "wait_hist_log2": [int(v) for v in hist]}},
                 "gpu_launches": args.steps, "clocks": clocks,
                 "status": lb.lb_strerror(status), "impl": "gb300"}
         print(json.dumps(line), flush=True)

@@ -180,6 +180,17 @@ LB_API int lb_series_start(lb_handle *h, int64_t capacity);
 LB_API int lb_series_read(lb_handle *h, double *out, int64_t max, int64_t *count);
 LB_API int lb_series_stop(lb_handle *h);
 
+/* Bursts of the recorded response (Sec. VIII, Fig. 14), analysed on the
+ * device.  Over the held record U_j (as lb_series_read returns it), with
+ * d_j = U_{j+1} - U_j and mu, sigma the mean and population standard
+ * deviation of d, step j is "above" when |d_j - mu| > c sigma; a burst is a
+ * maximal run of above steps, starting at its first step.  hist[b],
+ * b < nbins (1 <= nbins <= 64), counts the waits between successive burst
+ * starts in [2^b, 2^(b+1)) steps (the last bin also every longer wait);
+ * *events (may be NULL) is the number of bursts.  LB_EINVAL without a record,
+ * for c < 0 or nbins out of range.  Synchronises. */
+LB_API int lb_series_bursts(lb_handle *h, double c, int nbins, int64_t *hist, int64_t *events);
+
 /* Ageing overlap of Eq. (CORRE) (Sec. VII), order parameter phi = rho_A - rho_B.
  * lb_phi_snapshot stores phi(t_w) of the current state in the handle (FP64,
  * one device array of nx*ny doubles, kept until the next snapshot or
@@ -295,6 +306,18 @@ LB_API int lb_batch_get_state(lb_batch *b, int slot, double *f);
  * populations f (layout of lb_get_state; converted to the batch's storage),
  * keeping its step budget and step count.  Synchronises. */
 LB_API int lb_batch_set_state(lb_batch *b, int slot, const double *f);
+
+/* lb_series_start / lb_series_read / lb_series_stop of one replica: its U_k
+ * after every step it takes, in a device ring of `capacity` entries, kept
+ * while the batch runs (the 100-realisation response statistics of
+ * Sec. VIII come from these).  Start and stop synchronise and take effect
+ * from the next lb_batch_run; entry t is U_k of the replica's state at the
+ * start of its t-th step after the start. */
+LB_API int lb_batch_series_start(lb_batch *b, int slot, int64_t capacity);
+LB_API int lb_batch_series_read(lb_batch *b, int slot, double *out, int64_t max, int64_t *count);
+LB_API int lb_batch_series_stop(lb_batch *b, int slot);
+LB_API int lb_batch_series_bursts(lb_batch *b, int slot, double c, int nbins, int64_t *hist,
+                                  int64_t *events);
 /* lb_shear_diagnostics, lb_phi_snapshot and lb_phi_overlap of one replica
  * (synchronise; a replica's snapshot is freed with the replica). */
 LB_API int lb_batch_shear_diagnostics(lb_batch *b, int slot, double *u_k, double *i_ab);

@@ -336,67 +336,99 @@ extern "C" int lb_shear_diagnostics(lb_handle* h, double* u_k, double* i_ab) {
   return LB_OK;
 }
 
-static void series_free(lb_handle* h) {
-  cudaFree(h->sr.buf);
-  cudaFree(h->sr.t);
-  cudaFree(h->sr.done);
-  h->sr = Series{nullptr, nullptr, nullptr, 0, 0, 0u};
+// ---- shear-response record (shared with the batched replicas) ----
+
+namespace lbk {
+
+void series_release(Series& s) {
+  cudaFree(s.buf);
+  cudaFree(s.t);
+  cudaFree(s.done);
+  cudaFree(const_cast<void*>(s.wt));
+  s = Series{};
 }
+
+int series_alloc(int64_t capacity, int k, int ny, int storage, cudaStream_t st, Series* out) {
+  // (one spare entry: the last contribution of a step clears the next step's)
+  Series s{};
+  s.cap = (int)capacity + 1;
+  s.k = k >= 1 ? k : 1;
+  // the row weights sin(2 pi k y / ny), in FP64 and rounded to the arithmetic type
+  std::vector<double> w((size_t)ny);
+  for (int y = 0; y < ny; ++y) w[y] = sin(2.0 * M_PI * (double)s.k * (double)y / (double)ny);
+  std::vector<float> wf(w.begin(), w.end());
+  const bool dbl = storage == LB_F64;
+  const size_t wbytes = (size_t)ny * (dbl ? sizeof(double) : sizeof(float));
+  void* wt = nullptr;
+  if (cudaMalloc(&s.buf, (size_t)s.cap * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&s.t, sizeof(long long)) != cudaSuccess ||
+      cudaMalloc(&s.done, sizeof(unsigned)) != cudaSuccess || cudaMalloc(&wt, wbytes) != cudaSuccess) {
+    cudaGetLastError();
+    s.wt = wt;
+    series_release(s);
+    return LB_ENOMEM;
+  }
+  s.wt = wt;
+  if (cudaMemsetAsync(s.buf, 0, (size_t)s.cap * sizeof(double), st) != cudaSuccess ||
+      cudaMemsetAsync(s.t, 0, sizeof(long long), st) != cudaSuccess ||
+      cudaMemsetAsync(s.done, 0, sizeof(unsigned), st) != cudaSuccess ||
+      cudaMemcpyAsync(wt, dbl ? (const void*)w.data() : (const void*)wf.data(), wbytes,
+                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    series_release(s);
+    return LB_ECUDA;
+  }
+  *out = s;
+  return LB_OK;
+}
+
+int series_read(const Series& s, double scale, double* out, int64_t max, int64_t* count,
+                cudaStream_t st) {
+  long long t = 0;
+  if (cudaMemcpyAsync(&t, s.t, sizeof(t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return LB_ECUDA;
+  long long n = t < s.cap - 1 ? t : s.cap - 1;  // steps still held
+  if (n > max) n = max;
+  std::vector<double> ring((size_t)s.cap);
+  if (n > 0 && (cudaMemcpyAsync(ring.data(), s.buf, ring.size() * sizeof(double),
+                                cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess))
+    return LB_ECUDA;
+  // the most recent n steps, oldest first
+  for (long long j = 0; j < n; ++j) out[j] = scale * ring[(size_t)((t - n + j) % s.cap)];
+  if (count) *count = n;
+  return LB_OK;
+}
+
+}  // namespace lbk
 
 extern "C" int lb_series_start(lb_handle* h, int64_t capacity) {
   if (!h || capacity < 1 || capacity > (1LL << 30)) return LB_EINVAL;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LB_ECUDA;
   drop_graphs(h);  // the captured launches carry the old record
-  series_free(h);
-  // (one spare entry: the last contribution of a step clears the next step's)
-  Series s{nullptr, nullptr, nullptr, (int)capacity + 1, h->p.k_kolmo >= 1 ? h->p.k_kolmo : 1, 0u};
-  if (cudaMalloc(&s.buf, (size_t)s.cap * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&s.t, sizeof(long long)) != cudaSuccess ||
-      cudaMalloc(&s.done, sizeof(unsigned)) != cudaSuccess) {
-    cudaGetLastError();
-    cudaFree(s.buf);
-    cudaFree(s.t);
-    cudaFree(s.done);
-    return LB_ENOMEM;
-  }
-  if (cudaMemsetAsync(s.buf, 0, (size_t)s.cap * sizeof(double), h->stream) != cudaSuccess ||
-      cudaMemsetAsync(s.t, 0, sizeof(long long), h->stream) != cudaSuccess ||
-      cudaMemsetAsync(s.done, 0, sizeof(unsigned), h->stream) != cudaSuccess ||
-      cudaStreamSynchronize(h->stream) != cudaSuccess) {
-    cudaFree(s.buf);
-    cudaFree(s.t);
-    cudaFree(s.done);
-    return LB_ECUDA;
-  }
-  h->sr = s;
-  return LB_OK;
+  series_release(h->sr);
+  return series_alloc(capacity, h->p.k_kolmo, h->ny, h->p.storage, h->stream, &h->sr);
 }
 
 extern "C" int lb_series_read(lb_handle* h, double* out, int64_t max, int64_t* count) {
   if (!h || !h->sr.buf || max < 0 || (max > 0 && !out)) return LB_EINVAL;
-  long long t = 0;
-  if (cudaMemcpyAsync(&t, h->sr.t, sizeof(t), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
-      cudaStreamSynchronize(h->stream) != cudaSuccess)
-    return LB_ECUDA;
-  long long n = t < h->sr.cap - 1 ? t : h->sr.cap - 1;  // steps still held
-  if (n > max) n = max;
-  std::vector<double> ring((size_t)h->sr.cap);
-  if (n > 0 && (cudaMemcpyAsync(ring.data(), h->sr.buf, ring.size() * sizeof(double),
-                                cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
-                cudaStreamSynchronize(h->stream) != cudaSuccess))
-    return LB_ECUDA;
-  // the most recent n steps, oldest first, as U_k = (2 / (nx ny)) sum u_x sin(k y)
-  const double scale = 2.0 / ((double)h->nx * (double)h->ny);
-  for (long long j = 0; j < n; ++j) out[j] = scale * ring[(size_t)((t - n + j) % h->sr.cap)];
-  if (count) *count = n;
-  return LB_OK;
+  // U_k = (2 / (nx ny)) sum u_x sin(k y)
+  return series_read(h->sr, 2.0 / ((double)h->nx * (double)h->ny), out, max, count, h->stream);
+}
+
+extern "C" int lb_series_bursts(lb_handle* h, double c, int nbins, int64_t* hist,
+                                int64_t* events) {
+  if (!h || !h->sr.buf) return LB_EINVAL;
+  return series_bursts(h->sr, 2.0 / ((double)h->nx * (double)h->ny), c, nbins, hist, events,
+                       h->stream);
 }
 
 extern "C" int lb_series_stop(lb_handle* h) {
   if (!h) return LB_EINVAL;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LB_ECUDA;
   drop_graphs(h);
-  series_free(h);
+  series_release(h->sr);
   return LB_OK;
 }
 

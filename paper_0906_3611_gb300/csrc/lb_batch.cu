@@ -32,6 +32,7 @@ struct Slot {
   void* buf[2] = {nullptr, nullptr};
   double* phi_w = nullptr;  // ageing snapshot phi(t_w) (lazily allocated)
   void* body = nullptr;     // Kolmogorov body acceleration per row (nullptr: none)
+  Series sr{};              // shear-response record (sr.buf == nullptr: off)
 };
 
 void free_slot(Slot& s) {
@@ -39,6 +40,7 @@ void free_slot(Slot& s) {
   cudaFree(s.buf[1]);
   cudaFree(s.phi_w);
   cudaFree(s.body);
+  series_release(s.sr);
   s = Slot();
 }
 
@@ -74,6 +76,7 @@ struct lb_batch {
   alignas(16) unsigned char table[sizeof(PhysTable<double>)] = {};
   int nphys = 0;
   bool body = false;  // some replica has a Kolmogorov body-force table
+  bool rec = false;   // some replica keeps a shear-response record
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
 };
@@ -309,11 +312,15 @@ static int rebuild_items(lb_batch* b) {
     drop_graph(b);  // the captured launches point at the old list
   }
   b->n_items = (int)items.size();
-  bool body = false;
-  for (const Slot& s : b->slots) body = body || (s.used && s.body);
-  if (body != b->body) {
+  bool body = false, rec = false;
+  for (const Slot& s : b->slots) {
+    body = body || (s.used && s.body);
+    rec = rec || (s.used && s.sr.buf);
+  }
+  if (body != b->body || rec != b->rec) {
     b->body = body;
-    drop_graph(b);  // the captured launches use the other kernel variant
+    b->rec = rec;
+    drop_graph(b);  // the captured launches use another kernel variant
   }
   if (!items.empty() &&
       cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(WorkItem),
@@ -463,7 +470,7 @@ extern "C" int lb_batch_set_steps(lb_batch* b, int slot, int64_t steps) {
 
 static cudaError_t batch_launch(lb_batch* b, cudaStream_t st) {
   return launch_step_rows_batch(b->storage, b->d_reps, b->d_items, b->d_offsets, b->grid,
-                                b->table, b->nphys, b->body, b->d_status, st);
+                                b->table, b->nphys, b->body, b->rec, b->d_status, st);
 }
 
 static int ensure_batch_graph(lb_batch* b) {
@@ -752,6 +759,71 @@ extern "C" int lb_batch_set_state(lb_batch* b, int slot, const double* f) {
       return LB_ECUDA;
   }
   return cudaStreamSynchronize(b->stream) == cudaSuccess ? LB_OK : LB_ECUDA;
+}
+
+// Writes the record field of replica `slot` (stream-ordered, synchronises).
+static int write_series_field(lb_batch* b, int slot, const Series& sr) {
+  const size_t off = b->storage == LB_F64 ? offsetof(ReplicaDev<double>, sr)
+                                          : offsetof(ReplicaDev<float>, sr);
+  if (cudaMemcpyAsync((char*)b->d_reps + (size_t)slot * rep_bytes(b->storage) + off, &sr,
+                      sizeof(Series), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+      cudaStreamSynchronize(b->stream) != cudaSuccess)
+    return LB_ECUDA;
+  return LB_OK;
+}
+
+extern "C" int lb_batch_series_start(lb_batch* b, int slot, int64_t capacity) {
+  if (!b || slot < 0 || slot >= b->capacity || !b->slots[slot].used || capacity < 1 ||
+      capacity > (1LL << 30))
+    return LB_EINVAL;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return LB_ECUDA;
+  Slot& s = b->slots[slot];
+  const Series off{};
+  int rc = write_series_field(b, slot, off);  // (the old ring is no longer referenced)
+  if (rc) return rc;
+  series_release(s.sr);
+  b->dirty = true;  // the launch variant is chosen at the next work-list build
+  rc = series_alloc(capacity, s.p.k_kolmo, s.ny, s.p.storage, b->stream, &s.sr);
+  if (rc) return rc;
+  std::vector<unsigned char> recs;  // the replica's step count: the record's origin
+  int par;
+  long long rem;
+  rc = read_records(b, recs);
+  if (!rc) record_fields(b, recs.data() + (size_t)slot * rep_bytes(b->storage), &par, &rem,
+                         &s.sr.step);
+  if (!rc) rc = write_series_field(b, slot, s.sr);
+  if (rc) series_release(s.sr);
+  return rc;
+}
+
+extern "C" int lb_batch_series_read(lb_batch* b, int slot, double* out, int64_t max,
+                                    int64_t* count) {
+  if (!b || slot < 0 || slot >= b->capacity || !b->slots[slot].used || max < 0 ||
+      (max > 0 && !out))
+    return LB_EINVAL;
+  const Slot& s = b->slots[slot];
+  if (!s.sr.buf) return LB_EINVAL;
+  return series_read(s.sr, 2.0 / ((double)s.nx * (double)s.ny), out, max, count, b->stream);
+}
+
+extern "C" int lb_batch_series_bursts(lb_batch* b, int slot, double c, int nbins,
+                                      int64_t* hist, int64_t* events) {
+  if (!b || slot < 0 || slot >= b->capacity || !b->slots[slot].used) return LB_EINVAL;
+  const Slot& s = b->slots[slot];
+  if (!s.sr.buf) return LB_EINVAL;
+  return series_bursts(s.sr, 2.0 / ((double)s.nx * (double)s.ny), c, nbins, hist, events,
+                       b->stream);
+}
+
+extern "C" int lb_batch_series_stop(lb_batch* b, int slot) {
+  if (!b || slot < 0 || slot >= b->capacity || !b->slots[slot].used) return LB_EINVAL;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return LB_ECUDA;
+  const Series off{};
+  int rc = write_series_field(b, slot, off);
+  if (rc) return rc;
+  series_release(b->slots[slot].sr);
+  b->dirty = true;
+  return LB_OK;
 }
 
 extern "C" int lb_batch_autotune(lb_batch* b, int steps_per_candidate, int* layout,

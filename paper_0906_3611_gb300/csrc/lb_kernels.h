@@ -62,7 +62,25 @@ struct Series {
   int cap;
   int k;
   unsigned expected;  // contributions per step (warps of the row kernel, blocks of the tile kernel)
+  const void* wt;     // sin(2 pi k y / ny) of every row y, in the arithmetic type
+                      // (double for FP64 storage, else float)
+  long long step;     // batched replicas: the replica's step count when the record
+                      // started (host); in the kernel, the record's step of the launch
+                      // (with expected = 0: contributions only, and the CTA that
+                      // finishes the replica's step advances the record)
 };
+
+// A record's device ring: allocate one of `capacity` usable entries (zeroed)
+// with its row weights for a lattice of ny rows (synchronises), release it, and read its most recent entries, oldest first,
+// scaled by `scale` (synchronises).  Return LB_* codes.
+int series_alloc(int64_t capacity, int k, int ny, int storage, cudaStream_t st, Series* out);
+void series_release(Series& s);
+int series_read(const Series& s, double scale, double* out, int64_t max, int64_t* count,
+                cudaStream_t st);
+// Bursts of the record's derivative and the log2 histogram of the waits
+// between them, analysed on the device (lb_series.cu); synchronises.
+int series_bursts(const Series& sr, double scale, double c, int nbins, int64_t* hist,
+                  int64_t* events, cudaStream_t st);
 
 // Number of FP64 observables accumulated per block by the observe kernels:
 // {sum rho_A, sum rho_B, P_x, P_y, sum sigma_xy, wall_top, wall_bottom, 0}.

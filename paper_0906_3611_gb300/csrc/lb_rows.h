@@ -27,6 +27,8 @@ struct ReplicaDev {
   long long remaining; // steps left in the budget (<= 0: idle)
   long long t;         // steps taken since (re)initialisation
   unsigned int done;   // items finished in the current step
+  Series sr;           // shear-response record (sr.buf == nullptr: off); its `step`
+                       // and `expected` are the kernel's
 };
 
 // One work item: strip columns [x0, x1), output rows [ylo, yhi).
@@ -68,9 +70,10 @@ cudaError_t make_body_table(int storage, const PhysD& ph, int ny, void** out, cu
 // CTA c of the persistent grid works on items [offsets[c], offsets[c+1]);
 // `table` is a host PhysTable<float> (FP32 and 16-bit storages) or
 // PhysTable<double> (FP64) with `nphys` sets in use, copied into the launch's
-// parameters; `body`: some replica has a body-force table.
+// parameters; `body`: some replica has a body-force table; `rec`: some
+// replica keeps a shear-response record.
 cudaError_t launch_step_rows_batch(int storage, void* reps, const WorkItem* items,
                                    const int* offsets, int grid, const void* table, int nphys,
-                                   bool body, Status* status, cudaStream_t st);
+                                   bool body, bool rec, Status* status, cudaStream_t st);
 
 }  // namespace lbk

@@ -111,15 +111,16 @@ __device__ __forceinline__ C wall_term(int i, C rho_s, C Uw) {
 
 // Adds one contribution to the series entry of the current step and, for the
 // last contribution of the step, advances the step count and clears the next
-// entry.  Called by one thread per contributing warp (or block).
+// entry.  Called by one thread per contributing warp (or block).  No fence:
+// nothing in the launch reads what another contributor wrote (the entry is
+// only summed into, the counter is atomic), and the next step, which reads
+// the step count and fills the cleared entry, is the next launch.
 __device__ __forceinline__ void series_commit(const Series& sr, long long t, double v) {
   atomicAdd(&sr.buf[t % sr.cap], v);
-  __threadfence();
   if (atomicAdd(sr.done, 1u) == sr.expected - 1) {
     sr.buf[(t + 1) % sr.cap] = 0.0;
     *sr.t = t + 1;
     *sr.done = 0u;
-    __threadfence();
   }
 }
 

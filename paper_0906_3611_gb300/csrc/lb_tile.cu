@@ -120,9 +120,8 @@ __global__ void __launch_bounds__(TTHREADS)
     shifted_velocities<C>(ph, rho, jx, jy, Fx, Fy, vx, vy, bad);
     if (!OBSERVE && sr.buf) {  // shear response: u_x sin(2 pi k y / ny) of this site
       const C den = rho[0] * ph.omega[0] + rho[1] * ph.omega[1];
-      const long long m = (2LL * sr.k * y) % (2LL * g.ny);
       sval = (double)(div_c<C>(jx[0] * ph.omega[0] + jx[1] * ph.omega[1], den) *
-                      sinpi_c<C>((C)m / (C)g.ny));
+                      __ldg((const C*)sr.wt + y));
     }
 
     if (OBSERVE) {
@@ -468,7 +467,7 @@ template <int STORAGE>
 static cudaError_t observe_t(const void* src, const Geom& g, const PhysD& pd, Status* status,
                              double* partials, cudaStream_t st) {
   using S = Store<STORAGE>;
-  const Series none = {nullptr, nullptr, nullptr, 0, 0, 0u};
+  const Series none{};
   k_tile<STORAGE, true><<<tile_grid(g), TTHREADS, 0, st>>>(
       (const typename S::T*)src, nullptr, g, make_phys<typename S::C>(pd), status, partials, none);
   return cudaGetLastError();

@@ -25,13 +25,14 @@ ELEM_BYTES = {LB_F64: 8, LB_F32: 4, LB_BF16_DEV: 2, LB_F16_DEV: 2}
 # every entry point declared in include/lb.h
 EXPORTED = ["lb_state_bytes", "lb_create", "lb_create_on", "lb_init_random", "lb_step",
             "lb_observables", "lb_shear_diagnostics", "lb_series_start", "lb_series_read",
-            "lb_series_stop", "lb_phi_snapshot", "lb_phi_overlap",
+            "lb_series_stop", "lb_series_bursts", "lb_batch_series_bursts", "lb_phi_snapshot", "lb_phi_overlap",
             "lb_get_state", "lb_set_state",
             "lb_set_state_raw",
             "lb_get_state_raw", "lb_time", "lb_status", "lb_sync", "lb_destroy", "lb_strerror",
             "lb_observables_noalloc", "lb_batch_create", "lb_batch_add", "lb_batch_remove",
             "lb_batch_set_steps", "lb_batch_run", "lb_batch_poll", "lb_batch_observables",
-            "lb_batch_get_state", "lb_batch_set_state", "lb_batch_shear_diagnostics", "lb_batch_phi_snapshot",
+            "lb_batch_get_state", "lb_batch_set_state",
+            "lb_batch_series_start", "lb_batch_series_read", "lb_batch_series_stop", "lb_batch_shear_diagnostics", "lb_batch_phi_snapshot",
             "lb_batch_phi_overlap", "lb_batch_autotune",
             "lb_batch_status", "lb_batch_destroy"]
 
@@ -71,6 +72,12 @@ def _load():
         "lb_series_start": (ctypes.c_int, [vp, ctypes.c_int64]),
         "lb_series_read": (ctypes.c_int, [vp, dp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
         "lb_series_stop": (ctypes.c_int, [vp]),
+        "lb_series_bursts": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_int64),
+                                            ctypes.POINTER(ctypes.c_int64)]),
+        "lb_batch_series_bursts": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                                  ctypes.POINTER(ctypes.c_int64),
+                                                  ctypes.POINTER(ctypes.c_int64)]),
         "lb_phi_snapshot": (ctypes.c_int, [vp]),
         "lb_phi_overlap": (ctypes.c_int, [vp, dp, dp]),
         "lb_batch_phi_snapshot": (ctypes.c_int, [vp, ctypes.c_int]),
@@ -96,6 +103,10 @@ def _load():
         "lb_batch_observables": (ctypes.c_int, [vp, ctypes.c_int, dp, dp, dp, dp]),
         "lb_batch_get_state": (ctypes.c_int, [vp, ctypes.c_int, dp]),
         "lb_batch_set_state": (ctypes.c_int, [vp, ctypes.c_int, dp]),
+        "lb_batch_series_start": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int64]),
+        "lb_batch_series_read": (ctypes.c_int, [vp, ctypes.c_int, dp, ctypes.c_int64,
+                                                ctypes.POINTER(ctypes.c_int64)]),
+        "lb_batch_series_stop": (ctypes.c_int, [vp, ctypes.c_int]),
         "lb_batch_shear_diagnostics": (ctypes.c_int, [vp, ctypes.c_int, dp, dp]),
         "lb_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                              ctypes.POINTER(ctypes.c_int)]),
@@ -201,6 +212,21 @@ def lb_series_read(h: int, max_count: int) -> np.ndarray:
 
 def lb_series_stop(h: int) -> None:
     _check(_lib.lb_series_stop(h), "lb_series_stop")
+
+
+def _bursts(fn, name, args, nbins: int) -> dict:
+    hist = (ctypes.c_int64 * nbins)()
+    ev = ctypes.c_int64(0)
+    _check(fn(*args, nbins, hist, ctypes.byref(ev)), name)
+    return {"hist": np.array(list(hist), dtype=np.int64), "events": int(ev.value)}
+
+
+def lb_series_bursts(h: int, c: float, nbins: int) -> dict:
+    return _bursts(_lib.lb_series_bursts, "lb_series_bursts", (h, c), nbins)
+
+
+def lb_batch_series_bursts(b: int, slot: int, c: float, nbins: int) -> dict:
+    return _bursts(_lib.lb_batch_series_bursts, "lb_batch_series_bursts", (b, slot, c), nbins)
 
 
 def lb_phi_snapshot(h: int) -> None:
@@ -310,6 +336,22 @@ def lb_batch_get_state(b: int, slot: int, f: np.ndarray) -> None:
     _check(_lib.lb_batch_get_state(b, slot, _dp(f)), "lb_batch_get_state")
 
 
+def lb_batch_series_start(b: int, slot: int, capacity: int) -> None:
+    _check(_lib.lb_batch_series_start(b, slot, capacity), "lb_batch_series_start")
+
+
+def lb_batch_series_read(b: int, slot: int, max_count: int) -> np.ndarray:
+    out = np.zeros(max(max_count, 1))
+    n = ctypes.c_int64(0)
+    _check(_lib.lb_batch_series_read(b, slot, _dp(out), max_count, ctypes.byref(n)),
+           "lb_batch_series_read")
+    return out[:n.value].copy()
+
+
+def lb_batch_series_stop(b: int, slot: int) -> None:
+    _check(_lib.lb_batch_series_stop(b, slot), "lb_batch_series_stop")
+
+
 def lb_batch_set_state(b: int, slot: int, f: np.ndarray) -> None:
     f = np.ascontiguousarray(f, dtype=np.float64)
     _check(_lib.lb_batch_set_state(b, slot, _dp(f)), "lb_batch_set_state")
@@ -388,6 +430,10 @@ class Lattice:
     def series_stop(self):
         lb_series_stop(self.h)
         return self
+
+    def series_bursts(self, c: float = 3.0, nbins: int = 32) -> dict:
+        """Bursts of dU/dt in the record and the log2 histogram of their spacing."""
+        return lb_series_bursts(self.h, c, nbins)
 
     def phi_snapshot(self):
         """Store phi(t_w) = rho_A - rho_B of the current state (Eq. (CORRE))."""
@@ -497,6 +543,22 @@ class Batch:
         f = np.empty((2, 9, ny, nx))
         lb_batch_get_state(self.h, slot, f)
         return f
+
+    def series_start(self, slot: int, capacity: int):
+        """Record the replica's U_k after every step (device ring of `capacity`)."""
+        lb_batch_series_start(self.h, slot, capacity)
+        return self
+
+    def series(self, slot: int, max_count: int = 1 << 20) -> np.ndarray:
+        """The replica's recorded U_k, oldest first (R = U_k / U0)."""
+        return lb_batch_series_read(self.h, slot, max_count)
+
+    def series_stop(self, slot: int):
+        lb_batch_series_stop(self.h, slot)
+        return self
+
+    def series_bursts(self, slot: int, c: float = 3.0, nbins: int = 32) -> dict:
+        return lb_batch_series_bursts(self.h, slot, c, nbins)
 
     def set_state(self, slot: int, f: np.ndarray):
         """Replace the replica's state by FP64 populations [2][9][ny][nx]."""

@@ -209,3 +209,92 @@ def test_batch_with_forced_and_plain_replicas_coming_and_going(lb, monkeypatch):
     lat = lb.Lattice(160, 64, pp).init_random(2).step(64)
     assert np.array_equal(lat.get_state(), plain)
     lat.close()
+
+
+def test_batched_series_equal_the_lattice_alone(lb, monkeypatch):
+    """A replica's record equals the record of the same lattice run alone (the
+    states are identical; each compute warp sums its sites in the arithmetic
+    type, FP32 here, over the rows of its work item, and the batch cuts the
+    rows differently: 1e-6 of the largest entry); replicas without a record
+    and forced replicas without one run beside it; stopping ends the record."""
+    pf = lb.make_params(**STD07, storage=lb.LB_F32, rho_ref=(0.612, 0.612),
+                        init_kind=lb.LB_INIT_UNIFORM_NOISE, init=(0.612, 0.612, 0.01),
+                        g_kolmo=5e-5, k_kolmo=1)
+    pp = lb.make_params(**STD07, storage=lb.LB_F32, rho_ref=(0.612, 0.612),
+                        init_kind=lb.LB_INIT_UNIFORM_NOISE, init=(0.612, 0.612, 0.01))
+    b = lb.Batch(4, lb.LB_F32)
+    s1 = b.add(256, 128, pf, 1, 100)
+    s2 = b.add(128, 128, pf, 2, 100)
+    s3 = b.add(192, 64, pp, 3, 100)
+    b.run(4)
+    b.series_start(s1, 64).series_start(s3, 8)
+    b.run(40)  # two replayed 16-step graphs and 8 single launches
+    got1, got3 = b.series(s1), b.series(s3)
+    b.series_stop(s3)
+    b.run(3)
+    with pytest.raises(lb.LBError):
+        b.series(s3)
+    assert len(b.series(s1)) == 43
+    assert b.status() == lb.LB_OK
+    b.close()
+    assert len(got1) == 40 and len(got3) == 8
+    monkeypatch.setenv("LB_STEP_KERNEL", "rows")
+    for (nx, ny, p, seed, cap), got in (((256, 128, pf, 1, 64), got1), ((192, 64, pp, 3, 8), got3)):
+        lat = lb.Lattice(nx, ny, p).init_random(seed).step(4).series_start(cap).step(40)
+        ref = lat.series()
+        lat.close()
+        assert len(ref) == len(got)
+        assert np.max(np.abs(ref - got)) <= 1e-6 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("c", [0.5, 1.0])
+def test_burst_statistics_match_the_oracle(lb, c):
+    """lb_series_bursts / lb_batch_series_bursts equal oracle.response.bursts of
+    the same record, bit for bit: a wrapped ring of 4095 entries, four
+    analysis chunks, bursts across chunk edges.  (FP16 storage: its
+    stochastic rounding makes the recorded derivative jagged, so that there
+    are many bursts to compare.)"""
+    from oracle import response as RS
+    p = lb.make_params(**STD07, storage=lb.LB_F16_DEV, rho_ref=(0.612, 0.612),
+                       init_kind=lb.LB_INIT_UNIFORM_NOISE, init=(0.612, 0.612, 0.01),
+                       g_kolmo=2e-5, k_kolmo=1)
+    lat = lb.Lattice(128, 128, p).init_random(7).series_start(4095).step(5000)
+    U = lat.series()
+    got = lat.series_bursts(c, 12)
+    assert lat.status() == lb.LB_OK
+    lat.close()
+    assert len(U) == 4095
+    ref = RS.bursts(U, c, 12)
+    d = RS.derivative(U)
+    mu, th = RS.threshold(d, c)
+    assert np.min(np.abs(np.abs(d - mu) - th)) > 1e-9 * th  # no decision at the FP edge
+    assert got["events"] == ref["events"] > 10
+    assert np.array_equal(got["hist"], ref["hist"])
+    # the same replica in a batch
+    b = lb.Batch(2, lb.LB_F16_DEV)
+    s = b.add(128, 128, p, 7, 5000)
+    b.add(96, 64, p, 8, 5000)
+    b.series_start(s, 4095)
+    b.run(5000)
+    Ub, gb = b.series(s), b.series_bursts(s, c, 12)
+    b.close()
+    rb = RS.bursts(Ub, c, 12)
+    assert gb["events"] == rb["events"] and np.array_equal(gb["hist"], rb["hist"])
+
+
+def test_burst_statistics_of_short_records(lb):
+    p = lb.make_params(**STD07, storage=lb.LB_F32, rho_ref=(0.612, 0.612),
+                       g_kolmo=2e-5, k_kolmo=1)
+    lat = lb.Lattice(128, 64, p).init_random(1)
+    with pytest.raises(lb.LBError):
+        lat.series_bursts()  # no record
+    lat.series_start(100)
+    for steps in (0, 1, 2):  # fewer than two derivative samples: no bursts
+        r = lat.series_bursts(2.0, 4)
+        assert r["events"] == 0 and not r["hist"].any()
+        lat.step(1)
+    with pytest.raises(lb.LBError):
+        lat.series_bursts(-1.0, 4)
+    with pytest.raises(lb.LBError):
+        lat.series_bursts(2.0, 65)
+    lat.close()
