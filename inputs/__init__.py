@@ -34,3 +34,12 @@ def sample_sites(nx: int, ny: int, count: int, seed: int):
     while len(pts) < min(count, nx * ny):
         pts.add((int(g.integers(0, ny)), int(g.integers(0, nx))))
     return sorted(pts)
+
+
+def fill_device_uniform(t, seed: int, lo: float, hi: float) -> None:
+    """Fill a CUDA tensor in place with U(lo, hi) draws of torch's seeded
+    Philox generator (for lattices too large to stage from the host)."""
+    import torch
+    g = torch.Generator(device=t.device)
+    g.manual_seed(int(seed))
+    t.uniform_(lo, hi, generator=g)

@@ -227,11 +227,11 @@ def test_negative_density_is_flagged_like_the_oracle(lb):
     assert np.allclose(g, ref, rtol=1e-12, atol=1e-15)
 
 
-def _patch_reference(rho0f, ys, xs, ny, nx, phys, boundary, U, dtype, rho_ref=(0.0, 0.0)):
-    """One oracle step on a local patch around (ys, xs); returns the centre site's f.
-    The initial populations are w_i rho_ref,s + (w_i rho_s - w_i rho_ref,s) rounded
-    to `dtype`, as the deviation storages hold them."""
-    R = 5
+def _patch_rows_cols(ys, xs, ny, nx, boundary, R=5):
+    """Rows and columns of the (2R+1)^2 patch around (ys, xs), and the
+    boundary the patch is stepped with: the new populations of a site depend
+    only on the 7 x 7 box around it, so the centre of an 11 x 11 patch is
+    exact (at a Couette wall the patch ends at the wall)."""
     if boundary == 1 and ys < R:
         rows = np.arange(0, 2 * R + 1)
     elif boundary == 1 and ys > ny - 1 - R:
@@ -239,10 +239,19 @@ def _patch_reference(rho0f, ys, xs, ny, nx, phys, boundary, U, dtype, rho_ref=(0
     else:
         rows = (np.arange(ys - R, ys + R + 1)) % ny
     cols = (np.arange(xs - R, xs + R + 1)) % nx
+    pb = boundary if (boundary == 1 and (ys < R or ys > ny - 1 - R)) else 0
+    return rows, cols, pb
+
+
+def _patch_reference(rho0f, ys, xs, ny, nx, phys, boundary, U, dtype, rho_ref=(0.0, 0.0)):
+    """One oracle step on a local patch around (ys, xs); returns the centre site's f.
+    The initial populations are w_i rho_ref,s + (w_i rho_s - w_i rho_ref,s) rounded
+    to `dtype`, as the deviation storages hold them."""
+    R = 5
+    rows, cols, pb = _patch_rows_cols(ys, xs, ny, nx, boundary, R)
     rho = rho0f[:, rows][:, :, cols]
     base = W9[None, :, None, None] * np.asarray(rho_ref, dtype=np.float64)[:, None, None, None]
     f = base + (W9[None, :, None, None] * rho[:, None] - base).astype(dtype).astype(np.float64)
-    pb = boundary if (boundary == 1 and (ys < R or ys > ny - 1 - R)) else 0
     g, _ = oracle.step(f, _oracle_p(phys, pb, U), 1)
     cy = int(np.where(rows == ys)[0][0])
     return g[:, :, cy, R]
@@ -298,3 +307,51 @@ def test_tile_and_rows_kernels_agree(lb, monkeypatch):
         assert lat.status() == lb.LB_OK
         lat.close()
     assert _scaled_err(out["rows"], out["tile"]) <= 1e-11
+
+
+@pytest.mark.parametrize("n", [15424, 15456])
+def test_maximum_size_one_step_fp32(lb, n):
+    """The largest square lattice whose nine direction planes the row kernel
+    addresses with 32-bit offsets (15424^2: 9 * plane < 2^31 sites), and the
+    next size up, which runs on the tile kernel (64-bit offsets).  FP32
+    deviation storage, 2 x 17 GB, Couette U = 0.02, asymmetric couplings; the
+    state is drawn on the device (U(-1, 1) deviations of 5 % of w_i rho_ref)
+    and one step is compared on sampled sites with the oracle on 11 x 11
+    patches of that state (1e-5)."""
+    import torch
+    U = 0.02
+    rho_ref = np.float32([0.9, 0.45]).astype(np.float64)
+    lat = lb.Lattice(n, n, _params(lb, ASYM, lb.LB_F32, boundary=1, U=U, rho_ref=(0.9, 0.45)))
+    pitch = (n + 31) // 32 * 32
+    cnt = 9 * n * pitch * 2
+
+    def view(k):
+        return lat._bufs[k][:cnt * 4].view(torch.float32).view(9, n, pitch, 2)
+
+    v0 = view(0)
+    inputs.fill_device_uniform(v0, seed=n, lo=-1.0, hi=1.0)
+    scale = torch.tensor(W9[:, None] * rho_ref[None, :] * 0.05, dtype=torch.float32, device="cuda")
+    v0.mul_(scale[:, None, None, :])
+    sites = inputs.sample_sites(n, n, 12, seed=3) + [(0, 5), (n - 1, n - 1), (7, 0), (2500, n - 2)]
+    patches = []
+    for ys, xs in sites:
+        rows, cols, pb = _patch_rows_cols(ys, xs, n, n, 1)
+        ri = torch.as_tensor(rows, device="cuda")
+        ci = torch.as_tensor(cols, device="cuda")
+        d = v0.index_select(1, ri).index_select(2, ci).double().cpu().numpy()  # [9][11][11][2]
+        patches.append((ys, xs, rows, pb, d.transpose(3, 0, 1, 2)))
+    torch.cuda.synchronize()
+    lat.step(1).sync()
+    assert lat.status() == lb.LB_OK
+    v1 = view(1)
+    base = W9[None, :] * rho_ref[:, None]
+    for ys, xs, rows, pb, d in patches:
+        got = base + v1[:, ys, xs, :].double().cpu().numpy().T  # [2][9]
+        f = W9[None, :, None, None] * rho_ref[:, None, None, None] + d
+        g, bad = oracle.step(f, _oracle_p(ASYM, pb, U), 1)
+        assert bad == 0
+        ref = g[:, :, int(np.where(rows == ys)[0][0]), 5]
+        assert _rel_err(got, ref) <= 1e-5, (ys, xs)
+    lat.close()
+    del v0, v1, lat
+    torch.cuda.empty_cache()
