@@ -243,6 +243,7 @@ static int ensure_graph(lb_handle* h, int from) {
 
 extern "C" int lb_step(lb_handle* h, int64_t n) {
   if (!h || n < 0) return LB_EINVAL;
+  NvtxRange range("lb_step");
   int64_t left = n;
   if (left >= kGraphSteps) {
     int rc = ensure_graph(h, h->cur);

@@ -501,6 +501,7 @@ static int ensure_batch_graph(lb_batch* b) {
 
 extern "C" int lb_batch_run(lb_batch* b, int64_t n) {
   if (!b || n < 0) return LB_EINVAL;
+  NvtxRange range("lb_batch_run");
   if (b->dirty) {
     int rc = rebuild_items(b);
     if (rc) return rc;
@@ -829,6 +830,7 @@ extern "C" int lb_batch_series_stop(lb_batch* b, int slot) {
 extern "C" int lb_batch_autotune(lb_batch* b, int steps_per_candidate, int* layout,
                                  int* rows_per_item) {
   if (!b || steps_per_candidate < 1) return LB_EINVAL;
+  NvtxRange range("lb_batch_autotune");
   // (layout, longest piece): contiguous or packed work lists, uncut or cut
   const int cands[][2] = {{0, 1 << 30}, {0, 512}, {1, 1 << 30}, {1, 512}, {1, 128}};
   float best_ms = -1.0f;

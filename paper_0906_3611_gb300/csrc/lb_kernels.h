@@ -4,11 +4,21 @@
 
 #include <cuda_runtime.h>
 #include <math.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "lb_common.cuh"
 
 namespace lbk {
+
+// Scoped NVTX range around a host entry point (the range names the call on a
+// profiler's timeline; without a tool attached NVTX does nothing).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Physics constants in FP64, as prepared by the API layer from lb_params.
 struct PhysD {

@@ -7,7 +7,11 @@ admitted into free slots as long as their population buffers fit the HBM
 budget, every chunk of steps advances all admitted requests in one launch
 per step, each request stops on the device when its own step budget is
 spent, and finished requests are reduced (FP64 mass and stress), returned
-and their slots and memory freed before the next chunk.
+and their slots and memory freed before the next chunk.  A request can be
+cancelled (queued or running) and can carry a deadline, after which it is
+retired unfinished; an admission the device refuses (out of memory, no
+free slot) leaves the request queued until memory frees up, or fails it when
+nothing else holds memory.
 
 Scheduling only: every step of every request runs in liblb.so's kernels.
 """
@@ -31,6 +35,7 @@ class Request:
     boundary: int = lb.LB_PERIODIC
     U_wall: float = 0.0
     arrival: float = 0.0  # seconds after the start of the run
+    deadline: float | None = None  # seconds after the start of the run (None: none)
 
 
 @dataclasses.dataclass
@@ -41,9 +46,10 @@ class Result:
     arrival: float
     admitted: float
     finished: float
-    mass: np.ndarray
-    stress: np.ndarray
+    mass: np.ndarray | None
+    stress: np.ndarray | None
     state: np.ndarray | None = None
+    status: str = "done"  # done | cancelled | expired | failed
 
     @property
     def latency(self) -> float:
@@ -56,9 +62,7 @@ class Server:
     def __init__(self, phys: dict, storage: int = lb.LB_F32, capacity: int = 64,
                  budget_bytes: float = 150e9, chunk: int = 256, rho_ref=(0.88, 0.44),
                  init_kind: int = lb.LB_INIT_BERNOULLI, init=(0.7, 1.2, 0.1, 0.02),
-                 keep_state: bool = False, stream=None):
-        import torch
-
+                 keep_state: bool = False, stream=None, batch=None):
         self.phys = phys
         self.storage = storage
         self.capacity = capacity
@@ -68,12 +72,17 @@ class Server:
         self.init_kind = init_kind
         self.init = init
         self.keep_state = keep_state
-        self.stream = stream if stream is not None else torch.cuda.Stream()
-        self.batch = lb.Batch(capacity, storage, self.stream)
+        if batch is None:  # (a caller-supplied batch object stands in for the device one)
+            import torch
+            self.stream = stream if stream is not None else torch.cuda.Stream()
+            batch = lb.Batch(capacity, storage, self.stream)
+        self.batch = batch
         self.queue: collections.deque[Request] = collections.deque()
         self.active: dict[int, tuple[Request, float]] = {}  # slot -> (request, admitted)
         self.used = 0.0
         self.site_updates = 0
+        self.admission_failures = 0
+        self.retired: list[Result] = []  # cancelled / expired / failed, not yet returned
         self.t0 = time.perf_counter()
 
     def now(self) -> float:
@@ -92,19 +101,68 @@ class Server:
             raise ValueError(f"request {req.rid} needs more than the whole HBM budget")
         self.queue.append(req)
 
+    def _retire(self, req: Request, admitted: float, status: str, steps: int = 0):
+        self.retired.append(Result(req.rid, req.side, steps, req.arrival, admitted, self.now(),
+                                   None, None, None, status))
+
     def admit(self) -> int:
-        """Move queued requests into free slots while their memory fits (FIFO)."""
+        """Move queued requests into free slots while their memory fits (FIFO).
+        A refused admission (LB_ENOMEM, LB_EBUSY) keeps the request at the head
+        of the queue while other requests hold memory, and fails it otherwise."""
         n = 0
         while self.queue and len(self.active) < self.capacity:
             req = self.queue[0]
             need = self.bytes_of(req)
             if self.used + need > self.budget:
                 break
+            try:
+                slot = self.batch.add(req.side, req.side, self.params(req), req.seed, req.steps)
+            except lb.LBError as e:
+                if e.code not in (lb.LB_ENOMEM, lb.LB_EBUSY):
+                    raise
+                self.admission_failures += 1
+                if not self.active:  # nothing to wait for: it can never be admitted
+                    self.queue.popleft()
+                    self._retire(req, self.now(), "failed")
+                    continue
+                break
             self.queue.popleft()
-            slot = self.batch.add(req.side, req.side, self.params(req), req.seed, req.steps)
             self.active[slot] = (req, self.now())
             self.used += need
             n += 1
+        return n
+
+    def cancel(self, rid: int) -> bool:
+        """Withdraw request `rid`, queued or running; False if it is unknown or done."""
+        for req in list(self.queue):
+            if req.rid == rid:
+                self.queue.remove(req)
+                self._retire(req, self.now(), "cancelled")
+                return True
+        for slot, (req, admitted) in list(self.active.items()):
+            if req.rid == rid:
+                self._release(slot, req)
+                self._retire(req, admitted, "cancelled")
+                return True
+        return False
+
+    def _release(self, slot: int, req: Request):
+        self.batch.remove(slot)
+        del self.active[slot]
+        self.used -= self.bytes_of(req)
+
+    def expire(self) -> int:
+        """Retire every queued or running request whose deadline has passed."""
+        t, n = self.now(), 0
+        for req in [r for r in self.queue if r.deadline is not None and r.deadline <= t]:
+            self.queue.remove(req)
+            self._retire(req, t, "expired")
+            n += 1
+        for slot, (req, admitted) in list(self.active.items()):
+            if req.deadline is not None and req.deadline <= t:
+                self._release(slot, req)
+                self._retire(req, admitted, "expired")
+                n += 1
         return n
 
     def step_chunk(self) -> list[Result]:
@@ -124,9 +182,7 @@ class Server:
             state = self.batch.get_state(slot) if self.keep_state else None
             out.append(Result(req.rid, req.side, int(done[slot]), req.arrival, admitted, self.now(),
                               obs["mass"], obs["stress"], state))
-            self.batch.remove(slot)
-            del self.active[slot]
-            self.used -= self.bytes_of(req)
+            self._release(slot, req)
             self.site_updates += req.side * req.side * req.steps
         return out
 
@@ -141,11 +197,16 @@ class Server:
                 break
             while pending and pending[0].arrival <= t:
                 self.submit(pending.popleft())
+            self.expire()
             self.admit()
+            results.extend(self.retired)
+            self.retired = []
             if self.active:
                 results.extend(self.step_chunk())
             elif pending:
                 time.sleep(max(0.0, min(0.01, pending[0].arrival - self.now())))
+        results.extend(self.retired)
+        self.retired = []
         return results
 
     def close(self):
