@@ -355,3 +355,36 @@ def test_maximum_size_one_step_fp32(lb, n):
     lat.close()
     del v0, v1, lat
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-10), ("f32", 1e-4)])
+def test_mixture_shear_wave_with_unequal_tau(lb, storage, tol):
+    """tau_A = 0.6, tau_B = 1.6 (Sec. III footnote: the mixture relaxes with the
+    mass-weighted tau_bar): a sine shear wave on the row kernel decays like the
+    oracle's, U_k after 100 and 400 steps equal to tol."""
+    st = {"f64": lb.LB_F64, "f32": lb.LB_F32}[storage]
+    nx, ny, rho = 128, 64, (0.5, 0.5)
+    k = 2 * np.pi / ny
+    y = np.arange(ny)
+    ux = 1e-3 * np.sin(k * y)
+    cx = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+    cu = cx[None, :, None, None] * ux[None, None, :, None]
+    f = (W9[None, :, None, None] * np.asarray(rho)[:, None, None, None] * np.ones((2, 1, ny, nx))
+         * (1 + 3 * cu + 4.5 * cu ** 2 - 1.5 * (ux ** 2)[None, None, :, None]))
+    if storage == "f32":
+        f = f.astype(np.float32).astype(np.float64)
+    phys = dict(tau=(0.6, 1.6), rho0=1.0, G_AB=0.0, Ga=(0.0, 0.0), Gr=(0.0, 0.0))
+    lat = lb.Lattice(nx, ny, lb.make_params(**phys, storage=st, rho_ref=rho))
+    lat.set_state(f)
+    got = []
+    for n in (100, 300):
+        lat.step(n)
+        got.append(lat.shear_diagnostics()["U_k"])
+    assert lat.status() == lb.LB_OK
+    lat.close()
+    g1, _ = oracle.step(f[:, :, :, :4], dict(tau=(0.6, 1.6)), 100)
+    g2, _ = oracle.step(g1, dict(tau=(0.6, 1.6)), 300)
+    ref = [oracle.shear_diagnostics(g, dict(tau=(0.6, 1.6)))["U_k"] for g in (g1, g2)]
+    assert got == pytest.approx(ref, rel=tol)
+    nu = np.log(got[0] / got[1]) / (k * k * 300)
+    assert nu == pytest.approx((1.1 - 0.5) / 3.0, rel=6e-3)  # tau_bar = 1.1

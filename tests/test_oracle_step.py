@@ -58,14 +58,17 @@ def test_uniform_state_is_a_fixed_point():
     assert np.allclose(g, f, rtol=1e-15, atol=0)
 
 
-def _shear_wave_nu(tau, ny=64, nx=5, t1=200, t2=1000):
+def _shear_wave_nu(tau, ny=64, nx=5, t1=200, t2=1000, rho=(1.0, 1.0)):
+    """Decay rate / k^2 of a sine shear wave of a uniform mixture; `tau` is one
+    value or a (tau_A, tau_B) pair."""
     k = 2 * math.pi / ny
     y = np.arange(ny)
     ux = 1e-3 * np.sin(k * y)
     cu = CX[None, :, None, None] * ux[None, None, :, None]
     usq = (ux ** 2)[None, None, :, None]
-    f = W9[None, :, None, None] * np.ones((2, 1, ny, nx)) * (1 + 3 * cu + 4.5 * cu ** 2 - 1.5 * usq)
-    p = dict(tau=(tau, tau))
+    f = (W9[None, :, None, None] * np.asarray(rho, dtype=float)[:, None, None, None]
+         * np.ones((2, 1, ny, nx)) * (1 + 3 * cu + 4.5 * cu ** 2 - 1.5 * usq))
+    p = dict(tau=tuple(tau) if np.ndim(tau) else (tau, tau))
     g1, _ = oracle.step(f, p, t1)
     g2, _ = oracle.step(g1, p, t2 - t1)
 
@@ -84,6 +87,22 @@ def test_shear_wave_decay_gives_bgk_viscosity(tau):
         assert expect == pytest.approx(float(Fraction(GOLD["viscosity_tau1"]["nu"])))
     # O(k^2) lattice corrections at k = 2 pi/64
     assert nu == pytest.approx(expect, rel=3e-3)
+
+
+@pytest.mark.parametrize("taus,rho", [((0.8, 1.3), (0.7, 0.3)), ((0.6, 1.6), (0.5, 0.5))])
+def test_mixture_viscosity_follows_the_mass_weighted_tau(taus, rho):
+    """Unequal relaxation times (Sec. III footnote): the mixture relaxes with
+    tau_bar = (rho_A tau_A + rho_B tau_B) / rho, nu = (tau_bar - 1/2)/3, up to
+    O(k^2) (the deviation falls 4x when ny doubles); the harmonic mean, the
+    other plausible reading, is far off."""
+    rA, rB = rho
+    tau_bar = (rA * taus[0] + rB * taus[1]) / (rA + rB)
+    nu_bar = (tau_bar - 0.5) / 3.0
+    dev = [_shear_wave_nu(taus, ny=ny, t1=100, t2=400, rho=rho) / nu_bar - 1.0 for ny in (32, 64)]
+    assert abs(dev[1]) < 6e-3
+    assert dev[0] / dev[1] == pytest.approx(4.0, rel=0.05)
+    tau_h = (rA + rB) / (rA / taus[0] + rB / taus[1])
+    assert abs((tau_h - 0.5) / 3.0 / nu_bar - 1.0) > 10 * abs(dev[1])
 
 
 def test_couette_without_couplings_is_linear_with_wall_stress():
