@@ -44,6 +44,8 @@ BATCHES = {
     # name: (replicas, side choices, U range, storage)
     "batch256_f32": (256, (128, 256, 512, 1024), 0.05, 1),
     "batch256_f16dev": (256, (128, 256, 512, 1024), 0.05, 3),
+    # the same size mix at a quarter of the replicas (1.6 GB: the profiling case)
+    "batch64_f16dev": (64, (128, 256, 512, 1024), 0.05, 3),
 }
 SHEARS = {
     # name: (replicas, side, U0 (laminar amplitude of the Kolmogorov flow), storage)
