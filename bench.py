@@ -46,6 +46,7 @@ BATCHES = {
     "batch256_f16dev": (256, (128, 256, 512, 1024), 0.05, 3),
     # the same size mix at a quarter of the replicas (1.6 GB: the profiling case)
     "batch64_f16dev": (64, (128, 256, 512, 1024), 0.05, 3),
+    "batch64_f32": (64, (128, 256, 512, 1024), 0.05, 1),
 }
 SHEARS = {
     # name: (replicas, side, U0 (laminar amplitude of the Kolmogorov flow), storage)
