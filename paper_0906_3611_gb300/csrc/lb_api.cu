@@ -181,9 +181,7 @@ extern "C" void lb_destroy(lb_handle* h) {
   cudaFree(h->d_stage);
   cudaFree(h->d_phi_w);
   cudaFree(h->d_body);
-  cudaFree(h->sr.buf);
-  cudaFree(h->sr.t);
-  cudaFree(h->sr.done);
+  series_release(h->sr);
   if (h->h_out) cudaFreeHost(h->h_out);
   cudaGetLastError();
   delete h;

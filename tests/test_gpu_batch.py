@@ -54,9 +54,9 @@ REPLICAS = [  # nx, ny, physics, boundary, U, seed, budget
 ]
 
 
-@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16", "f64"])
 def test_batch_equals_each_replica_alone(lb, monkeypatch, storage):
-    st = {"f32": lb.LB_F32, "f16": lb.LB_F16_DEV}[storage]
+    st = {"f32": lb.LB_F32, "f16": lb.LB_F16_DEV, "bf16": lb.LB_BF16_DEV, "f64": lb.LB_F64}[storage]
     b = lb.Batch(8, st)
     slots = [b.add(nx, ny, _p(lb, ph, st, bd, U), seed, steps)
              for nx, ny, ph, bd, U, seed, steps in REPLICAS]
