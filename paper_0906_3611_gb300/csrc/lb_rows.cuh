@@ -232,7 +232,7 @@ struct RowsLoop {
   static constexpr int SLOT = 9 * SW;
 
   const T2* __restrict__ src;
-  const Geom& g;
+  const Geom g;  // (a copy: the batched kernel holds the replica's geometry in shared memory)
   const Phys<C>& ph;
   const RowsSmem<STORAGE>& sm;
   int* s_abort;
