@@ -98,6 +98,11 @@ struct Phys {
   C Uwall;       // Couette wall speed
   C gk;          // Kolmogorov body acceleration amplitude (0: off)
   C kk;          // its wave number
+  // FP32 arithmetic: the per-species constants again as adjacent (A, B)
+  // pairs, so that packed arithmetic can take them from the parameter space
+  // instead of registers: 0..4 Wpsi, 5..7 W2psi, 8 rho_ref, 9 -rho0 E,
+  // 10 omega (one unused pair for FP64, which keeps them in registers)
+  alignas(2 * sizeof(C)) C pr[sizeof(C) == 4 ? 11 : 1][2];
 };
 
 template <typename C>

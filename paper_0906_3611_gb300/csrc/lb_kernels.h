@@ -176,6 +176,17 @@ inline Phys<C> make_phys(const PhysD& d) {
   p.Uwall = (C)d.U;
   p.gk = (C)d.gk;
   p.kk = (C)d.kk;
+  if constexpr (sizeof(C) == 4) {
+    for (int s = 0; s < 2; ++s) {
+      for (int k = 0; k < 5; ++k) p.pr[k][s] = p.Wpsi[s][k];
+      for (int k = 0; k < 3; ++k) p.pr[5 + k][s] = p.W2psi[s][k];
+      p.pr[8][s] = p.rho_ref[s];
+      p.pr[9][s] = -p.rho0 * p.E[s];  // (as the kernels form it in C)
+      p.pr[10][s] = p.omega[s];
+    }
+  } else {
+    p.pr[0][0] = p.pr[0][1] = C(0);
+  }
   return p;
 }
 

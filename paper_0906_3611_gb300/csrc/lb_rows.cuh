@@ -51,28 +51,31 @@ constexpr int WEXT = 32 + 4;  // a compute warp's row buffer: 32 columns + 2 + 2
 // PIPE: form the next row's rho/psi together with the current collision
 // (hides latency; costs live registers); LAG: carry each row's drho/psi in
 // registers until its collision (else the collision recomputes them from the
-// populations it re-reads: ~13 more instructions, 12 fewer live registers).
+// populations it re-reads: ~13 more instructions, 12 fewer live registers);
+// CPAR: take the per-species constants (stencil weights, rho_ref, omega) from
+// the parameter space at each use instead of holding them in 22 registers
+// (lets the 16-bit loops run 4 CTAs per SM; costs the FP32 loop 2 %).
 template <int STORAGE>
 struct RowsCfg;
 template <>
 struct RowsCfg<LB_F64> {
   static constexpr int NCW = 4, SOFF = 2, NSLOT = 5, MINB = 2;  // 16-byte pairs
-  static constexpr bool PIPE = true, LAG = true;
+  static constexpr bool PIPE = true, LAG = true, CPAR = false;
 };
 template <>
 struct RowsCfg<LB_F32> {
   static constexpr int NCW = 4, SOFF = 2, NSLOT = 7, MINB = 3;  // 8-byte pairs
-  static constexpr bool PIPE = true, LAG = true;
+  static constexpr bool PIPE = true, LAG = true, CPAR = false;
 };
 template <>
 struct RowsCfg<LB_BF16_DEV> {
-  static constexpr int NCW = 4, SOFF = 4, NSLOT = 8, MINB = 3;  // 4-byte pairs
-  static constexpr bool PIPE = false, LAG = true;
+  static constexpr int NCW = 4, SOFF = 4, NSLOT = 8, MINB = 4;  // 4-byte pairs
+  static constexpr bool PIPE = false, LAG = true, CPAR = true;
 };
 template <>
 struct RowsCfg<LB_F16_DEV> {
-  static constexpr int NCW = 4, SOFF = 4, NSLOT = 8, MINB = 3;
-  static constexpr bool PIPE = false, LAG = true;
+  static constexpr int NCW = 4, SOFF = 4, NSLOT = 8, MINB = 4;
+  static constexpr bool PIPE = false, LAG = true, CPAR = true;
 };
 
 template <int STORAGE>
@@ -249,7 +252,22 @@ struct RowsLoop {
   T2 *Pm, *P0, *Pp;
   P* wbuf;  // this warp's row buffer: [0, WEXT) rho, [WEXT, 2 WEXT) psi
   // per-species constants as pairs
-  P Wa, Wb, Wc, Wd, We, W2c, W2d, W2e, rho_ref, mrho0E, om;
+  P Wa_, Wb_, Wc_, Wd_, We_, W2c_, W2d_, W2e_, rho_ref_, mrho0E_, om_;  // (unless CPAR)
+  static constexpr bool CPAR = RowsCfg<STORAGE>::CPAR;
+  __device__ __forceinline__ P cpair(int k) const {  // pair k of the parameter space
+    return *reinterpret_cast<const P*>(ph.pr[k]);
+  }
+  __device__ __forceinline__ P Wa() const { return CPAR ? cpair(0) : Wa_; }
+  __device__ __forceinline__ P Wb() const { return CPAR ? cpair(1) : Wb_; }
+  __device__ __forceinline__ P Wc() const { return CPAR ? cpair(2) : Wc_; }
+  __device__ __forceinline__ P Wd() const { return CPAR ? cpair(3) : Wd_; }
+  __device__ __forceinline__ P We() const { return CPAR ? cpair(4) : We_; }
+  __device__ __forceinline__ P W2c() const { return CPAR ? cpair(5) : W2c_; }
+  __device__ __forceinline__ P W2d() const { return CPAR ? cpair(6) : W2d_; }
+  __device__ __forceinline__ P W2e() const { return CPAR ? cpair(7) : W2e_; }
+  __device__ __forceinline__ P rho_ref() const { return CPAR ? cpair(8) : rho_ref_; }
+  __device__ __forceinline__ P mrho0E() const { return CPAR ? cpair(9) : mrho0E_; }
+  __device__ __forceinline__ P om() const { return CPAR ? cpair(10) : om_; }
   // windows (see above) and loop state
   P Sx[5], Sy[5], Cx[5], Cy[5], lag_drho[5], lag_psi[5];
   int bad;
@@ -276,17 +294,19 @@ struct RowsLoop {
     Pp = dst + xp;
     plane = (int)g.plane;
     wbuf = sm.rowbuf + (warp < NCW ? warp : 0) * 2 * WEXT;
-    Wa = pmk(ph.Wpsi[0][0], ph.Wpsi[1][0]);
-    Wb = pmk(ph.Wpsi[0][1], ph.Wpsi[1][1]);
-    Wc = pmk(ph.Wpsi[0][2], ph.Wpsi[1][2]);
-    Wd = pmk(ph.Wpsi[0][3], ph.Wpsi[1][3]);
-    We = pmk(ph.Wpsi[0][4], ph.Wpsi[1][4]);
-    W2c = pmk(ph.W2psi[0][0], ph.W2psi[1][0]);
-    W2d = pmk(ph.W2psi[0][1], ph.W2psi[1][1]);
-    W2e = pmk(ph.W2psi[0][2], ph.W2psi[1][2]);
-    rho_ref = pmk(ph.rho_ref[0], ph.rho_ref[1]);
-    mrho0E = pmk(-ph.rho0 * ph.E[0], -ph.rho0 * ph.E[1]);
-    om = pmk(ph.omega[0], ph.omega[1]);
+    if (!CPAR) {
+      Wa_ = pmk(ph.Wpsi[0][0], ph.Wpsi[1][0]);
+      Wb_ = pmk(ph.Wpsi[0][1], ph.Wpsi[1][1]);
+      Wc_ = pmk(ph.Wpsi[0][2], ph.Wpsi[1][2]);
+      Wd_ = pmk(ph.Wpsi[0][3], ph.Wpsi[1][3]);
+      We_ = pmk(ph.Wpsi[0][4], ph.Wpsi[1][4]);
+      W2c_ = pmk(ph.W2psi[0][0], ph.W2psi[1][0]);
+      W2d_ = pmk(ph.W2psi[0][1], ph.W2psi[1][1]);
+      W2e_ = pmk(ph.W2psi[0][2], ph.W2psi[1][2]);
+      rho_ref_ = pmk(ph.rho_ref[0], ph.rho_ref[1]);
+      mrho0E_ = pmk(-ph.rho0 * ph.E[0], -ph.rho0 * ph.E[1]);
+      om_ = pmk(ph.omega[0], ph.omega[1]);
+    }
 #pragma unroll
     for (int k = 0; k < 5; ++k)
       Sx[k] = Sy[k] = Cx[k] = Cy[k] = lag_drho[k] = lag_psi[k] = pbc(C(0));
@@ -333,7 +353,7 @@ struct RowsLoop {
     for (int i = 0; i < 9; ++i) v[i] = PS::ld(p[i * SW]);
     const P a = sum9(v);
     drho = a;
-    rho = padd(rho_ref, a);
+    rho = padd(rho_ref(), a);
     psi = psi_of(a);
   }
   // pairwise sum of a site's nine populations (a shorter dependency chain than
@@ -344,7 +364,7 @@ struct RowsLoop {
   }
   __device__ __forceinline__ P psi_of(P drho) const {
     const P ex = pmk(exp_c<C>(-drho.x * ph.inv_rho0), exp_c<C>(-drho.y * ph.inv_rho0));
-    return pfma(mrho0E, ex, pbc(ph.rho0));
+    return pfma(mrho0E(), ex, pbc(ph.rho0));
   }
 
   // Row r's contribution to the force stencil of rows r-2 .. r+2, with the
@@ -358,11 +378,11 @@ struct RowsLoop {
     const P* pp = buf + WEXT;
     const P m2 = pp[e - 2], m1 = pp[e - 1], p1 = pp[e + 1], p2 = pp[e + 2];
     const P D1 = psub(p1, m1), D2 = psub(p2, m2), P1 = padd(p1, m1), P2 = padd(p2, m2);
-    const P T0 = pfma(Wa, D1, pmul(W2c, D2));
-    const P T1 = pfma(Wb, D1, pmul(W2d, D2));
-    const P T2v = pfma(Wd, D1, pmul(W2e, D2));
-    const P H1 = pfma(Wa, my_psi, pfma(Wb, P1, pmul(Wd, P2)));
-    const P H2 = pfma(Wc, my_psi, pfma(Wd, P1, pmul(We, P2)));
+    const P T0 = pfma(Wa(), D1, pmul(W2c(), D2));
+    const P T1 = pfma(Wb(), D1, pmul(W2d(), D2));
+    const P T2v = pfma(Wd(), D1, pmul(W2e(), D2));
+    const P H1 = pfma(Wa(), my_psi, pfma(Wb(), P1, pmul(Wd(), P2)));
+    const P H2 = pfma(Wc(), my_psi, pfma(Wd(), P1, pmul(We(), P2)));
     Sx[k0] = padd(Sx[k0], T2v);
     Sx[k1] = padd(Sx[k1], T1);
     Sx[k2] = padd(Sx[k2], T0);
@@ -590,7 +610,7 @@ struct RowsLoop {
       drho = sum9(d);
       psi0 = psi_of(drho);
     }
-    const P rho = padd(rho_ref, drho);
+    const P rho = padd(rho_ref(), drho);
     rho_out = rho;
     // G = -F: F_s = -psi_s S_s - rho_s C_s (+ rho_s gb along x, the body force)
     const P Gx = pfma(rho, pbc(-gb), pfma(psi0, Sx0, pmul(rho, Cx0)));
@@ -598,7 +618,7 @@ struct RowsLoop {
     const P jx = padd(padd(psub(d[1], d[3]), psub(d[5], d[6])), psub(d[8], d[7]));
     const P jy = padd(padd(psub(d[2], d[4]), psub(d[5], d[8])), psub(d[6], d[7]));
     // common velocity u = sum_s j_s/tau_s / sum_s rho_s/tau_s
-    const P rw = pmul(rho, om), jxw = pmul(jx, om), jyw = pmul(jy, om);
+    const P rw = pmul(rho, om()), jxw = pmul(jx, om()), jyw = pmul(jy, om());
     const C inv = div_c<C>(C(1), rw.x + rw.y);
     const C ux = (jxw.x + jxw.y) * inv, uy = (jyw.x + jyw.y) * inv;
     ux_out = ux;
@@ -613,16 +633,16 @@ struct RowsLoop {
     const P vy = pfma(k, Gy, pbc(uy));
     // BGK relaxation toward the shifted equilibrium (factored form, see lb_site.cuh)
     {
-      const P keep = psub(pbc(C(1)), om);
+      const P keep = psub(pbc(C(1)), om());
       const P v2 = pfma(vx, vx, pmul(vy, vy));
       const P tt = pfma(pmul(pbc(C(-1.5)), rho), v2, drho);
-      const P B0 = pmul(pmul(om, pbc(wq<C>(0))), tt);
-      const P B1 = pmul(pmul(om, pbc(wq<C>(1))), tt);
-      const P B2 = pmul(pmul(om, pbc(wq<C>(5))), tt);
-      const P a1 = pmul(pmul(om, pbc(C(3) * wq<C>(1))), rho);
-      const P b1 = pmul(pmul(om, pbc(C(4.5) * wq<C>(1))), rho);
-      const P a2 = pmul(pmul(om, pbc(C(3) * wq<C>(5))), rho);
-      const P b2 = pmul(pmul(om, pbc(C(4.5) * wq<C>(5))), rho);
+      const P B0 = pmul(pmul(om(), pbc(wq<C>(0))), tt);
+      const P B1 = pmul(pmul(om(), pbc(wq<C>(1))), tt);
+      const P B2 = pmul(pmul(om(), pbc(wq<C>(5))), tt);
+      const P a1 = pmul(pmul(om(), pbc(C(3) * wq<C>(1))), rho);
+      const P b1 = pmul(pmul(om(), pbc(C(4.5) * wq<C>(1))), rho);
+      const P a2 = pmul(pmul(om(), pbc(C(3) * wq<C>(5))), rho);
+      const P b2 = pmul(pmul(om(), pbc(C(4.5) * wq<C>(5))), rho);
       d[0] = pfma(keep, d[0], B0);
       const P ex = pfma(pmul(b1, vx), vx, B1), ax = pmul(a1, vx);
       const P ey = pfma(pmul(b1, vy), vy, B1), ay = pmul(a1, vy);
