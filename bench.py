@@ -421,7 +421,7 @@ def run_batch(args):
                            "sides": sorted(set(s for s, _, _ in reps)),
                            "storage": STORAGE_NAME[storage], "boundary": "couette",
                            "U_wall": "uniform[0, 0.05]",
-                           "work_list": {"layout": ["contiguous", "packed"][layout],
+                           "work_list": {"layout": ["contiguous", "packed", "waves"][layout],
                                          "max_piece_rows": rows},
                            "l2": f"inputs larger than L2 ({sites * 18 * es / 1e9:.1f} GB per buffer set)"},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -505,7 +505,7 @@ def run_shear(args):
                            "couplings": "rho0 = 0.7 standard set", "U0": U0, "g_kolmo": g,
                            "storage": STORAGE_NAME[storage],
                            "record": "U_k of every timed step, per replica, on the device",
-                           "work_list": {"layout": ["contiguous", "packed"][layout],
+                           "work_list": {"layout": ["contiguous", "packed", "waves"][layout],
                                          "max_piece_rows": rows},
                            "l2": f"{sites * 18 * es / 1e6:.0f} MB read per step: partly "
                                  "L2-resident (129 MB L2); not a bandwidth headline"},

@@ -325,11 +325,13 @@ LB_API int lb_batch_phi_snapshot(lb_batch *b, int slot);
 LB_API int lb_batch_phi_overlap(lb_batch *b, int slot, double *num, double *den);
 
 /* Pick the work-list layout and piece length that time fastest on the
- * current replicas, among five candidates: layout 0 deals the strip-rows of
+ * current replicas, among eight candidates: layout 0 deals the strip-rows of
  * all replicas out to the CTAs in contiguous equal shares (balanced whatever
- * the sizes); layout 1 cuts every replica into strips x equal row ranges and
- * packs them into the CTAs (neighbouring strips advance together and share
- * halos through L2); each uncut or with ranges cut at 512 or 128 rows.  Each
+ * the sizes), uncut or cut at 512 rows; layout 1 cuts every replica into
+ * strips x equal row ranges and packs them into the CTAs, uncut or with
+ * ranges of at most 512 or 128 rows; layout 2 cuts the same pieces (at most
+ * 512, 256 or 128 rows) and runs them in waves of one piece per CTA, the
+ * strips of a range side by side (they share halos through L2).  Each
  * candidate runs steps_per_candidate + 1 real steps of every replica with
  * budget left (spending that budget).  *layout and *rows_per_item receive the
  * choice (either may be NULL); the batch keeps it until the next call. */

@@ -67,7 +67,7 @@ struct lb_batch {
   double* h_out = nullptr;
   double* d_stage = nullptr;
   size_t stage_bytes = 0;
-  int layout = 0;                    // work-list layout (autotuned): 0 contiguous, 1 packed
+  int layout = 0;                    // work-list layout (autotuned): 0 contiguous, 1 packed, 2 waves
   int rows_per_item = 1 << 30;       // longest piece (autotuned); default: no cut
   int grid = 0;
   bool dirty = true;
@@ -286,11 +286,53 @@ static void build_contiguous(lb_batch* b, std::vector<WorkItem>& items, std::vec
   for (int c = cta + 1; c <= b->grid; ++c) offsets[c] = (int)items.size();
 }
 
+// Work list, wave layout.  Every used replica is cut, as the single-lattice
+// kernel cuts a lattice, into its 128-column strips times ceil(ny / h) equal
+// row ranges (h = rows_per_item); the pieces are listed tallest replica
+// first, range-major, and piece i becomes item i / G of CTA i mod G.  The G
+// pieces of a wave run side by side, so the strips of a range are staged at
+// the same time by neighbouring CTAs and share their halo columns and the
+// sectors at the strip edges through L2; the last, partial wave leaves some
+// CTAs one piece short.
+static void build_waves(lb_batch* b, std::vector<WorkItem>& items, std::vector<int>& offsets,
+                        std::vector<int>& counts) {
+  const int width = rows_strip_width(b->storage);
+  const long long h = std::max<long long>(1, b->rows_per_item);
+  std::vector<int> order;
+  for (int k = 0; k < b->capacity; ++k)
+    if (b->slots[k].used) order.push_back(k);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int c) { return b->slots[a].ny > b->slots[c].ny; });
+  std::vector<WorkItem> pieces;
+  for (int k : order) {
+    const Slot& s = b->slots[k];
+    const int nstrips = rows_nstrips(s.nx, width);
+    long long kr = (s.ny + h - 1) / h;
+    if (kr > s.ny) kr = s.ny;
+    for (long long q = 0; q < kr; ++q) {
+      const int ylo = (int)(q * s.ny / kr), yhi = (int)((q + 1) * s.ny / kr);
+      for (int j = 0; j < nstrips; ++j) {
+        pieces.push_back(WorkItem{k, rows_strip_x0(j, nstrips, s.nx, width),
+                                  rows_strip_x0(j + 1, nstrips, s.nx, width), ylo, yhi});
+        ++counts[k];
+      }
+    }
+  }
+  const size_t G = (size_t)b->grid;
+  for (size_t c = 0; c < G; ++c) {
+    offsets[c] = (int)items.size();
+    for (size_t i = c; i < pieces.size(); i += G) items.push_back(pieces[i]);
+  }
+  offsets[G] = (int)items.size();
+}
+
 static int rebuild_items(lb_batch* b) {
   std::vector<WorkItem> items;
   std::vector<int> offsets(b->grid + 1, 0);
   std::vector<int> counts(b->capacity, 0);
-  if (b->layout == 1)
+  if (b->layout == 2)
+    build_waves(b, items, offsets, counts);
+  else if (b->layout == 1)
     build_packed(b, items, offsets, counts);
   else
     build_contiguous(b, items, offsets, counts);
@@ -832,7 +874,8 @@ extern "C" int lb_batch_autotune(lb_batch* b, int steps_per_candidate, int* layo
   if (!b || steps_per_candidate < 1) return LB_EINVAL;
   NvtxRange range("lb_batch_autotune");
   // (layout, longest piece): contiguous or packed work lists, uncut or cut
-  const int cands[][2] = {{0, 1 << 30}, {0, 512}, {1, 1 << 30}, {1, 512}, {1, 128}};
+  const int cands[][2] = {{0, 1 << 30}, {0, 512}, {1, 1 << 30}, {1, 512},
+                          {1, 128},    {2, 512}, {2, 256},     {2, 128}};
   float best_ms = -1.0f;
   int best_l = b->layout, best_r = b->rows_per_item;
   cudaEvent_t e0, e1;

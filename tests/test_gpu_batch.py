@@ -108,12 +108,13 @@ def test_slots_are_reused_after_remove(lb, monkeypatch):
 def test_autotune_keeps_results_exact(lb, monkeypatch):
     b = lb.Batch(4, lb.LB_F32)
     k = b.add(512, 256, _p(lb, CFG, lb.LB_F32, 1, 0.02), 7, 1000)
-    layout, rows = b.autotune(2)  # 5 candidates x (2 + 1) steps
-    assert (layout, rows) in ((0, 1 << 30), (0, 512), (1, 1 << 30), (1, 512), (1, 128))
+    layout, rows = b.autotune(2)  # 8 candidates x (2 + 1) steps
+    assert (layout, rows) in ((0, 1 << 30), (0, 512), (1, 1 << 30), (1, 512), (1, 128),
+                              (2, 512), (2, 256), (2, 128))
     b.run(5)
     rem, done = b.poll()
     n = int(done[k])
-    assert n == 5 * 3 + 5
+    assert n == 8 * 3 + 5
     got = b.get_state(k)
     obs = b.observables(k)
     b.close()
