@@ -337,6 +337,12 @@ LB_API int lb_batch_phi_overlap(lb_batch *b, int slot, double *num, double *den)
  * choice (either may be NULL); the batch keeps it until the next call. */
 LB_API int lb_batch_autotune(lb_batch *b, int steps_per_candidate, int *layout, int *rows_per_item);
 
+/* Set the work-list layout (0 contiguous, 1 packed, 2 waves; see
+ * lb_batch_autotune) and the longest piece in rows (>= 1) directly, for
+ * batches whose replicas change too often to autotune; takes effect at the
+ * next lb_batch_run.  Default: 0, uncut. */
+LB_API int lb_batch_set_layout(lb_batch *b, int layout, int rows_per_item);
+
 /* Read and clear the batch's device status word (as lb_status). */
 LB_API int lb_batch_status(lb_batch *b);
 

@@ -869,6 +869,14 @@ extern "C" int lb_batch_series_stop(lb_batch* b, int slot) {
   return LB_OK;
 }
 
+extern "C" int lb_batch_set_layout(lb_batch* b, int layout, int rows_per_item) {
+  if (!b || layout < 0 || layout > 2 || rows_per_item < 1) return LB_EINVAL;
+  b->layout = layout;
+  b->rows_per_item = rows_per_item;
+  b->dirty = true;  // the next run rebuilds the work list
+  return LB_OK;
+}
+
 extern "C" int lb_batch_autotune(lb_batch* b, int steps_per_candidate, int* layout,
                                  int* rows_per_item) {
   if (!b || steps_per_candidate < 1) return LB_EINVAL;

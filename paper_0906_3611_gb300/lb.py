@@ -33,7 +33,7 @@ EXPORTED = ["lb_state_bytes", "lb_create", "lb_create_on", "lb_init_random", "lb
             "lb_batch_set_steps", "lb_batch_run", "lb_batch_poll", "lb_batch_observables",
             "lb_batch_get_state", "lb_batch_set_state",
             "lb_batch_series_start", "lb_batch_series_read", "lb_batch_series_stop", "lb_batch_shear_diagnostics", "lb_batch_phi_snapshot",
-            "lb_batch_phi_overlap", "lb_batch_autotune",
+            "lb_batch_phi_overlap", "lb_batch_autotune", "lb_batch_set_layout",
             "lb_batch_status", "lb_batch_destroy"]
 
 
@@ -108,6 +108,7 @@ def _load():
                                                 ctypes.POINTER(ctypes.c_int64)]),
         "lb_batch_series_stop": (ctypes.c_int, [vp, ctypes.c_int]),
         "lb_batch_shear_diagnostics": (ctypes.c_int, [vp, ctypes.c_int, dp, dp]),
+        "lb_batch_set_layout": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
         "lb_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                              ctypes.POINTER(ctypes.c_int)]),
         "lb_batch_status": (ctypes.c_int, [vp]),
@@ -364,6 +365,10 @@ def lb_batch_shear_diagnostics(b: int, slot: int) -> tuple[float, float]:
     return float(uk[0]), float(iab[0])
 
 
+def lb_batch_set_layout(b: int, layout: int, rows_per_item: int) -> None:
+    _check(_lib.lb_batch_set_layout(b, layout, rows_per_item), "lb_batch_set_layout")
+
+
 def lb_batch_autotune(b: int, steps_per_candidate: int) -> tuple[int, int]:
     layout = ctypes.c_int(0)
     rows = ctypes.c_int(0)
@@ -578,6 +583,11 @@ class Batch:
 
     def phi_overlap(self, slot: int) -> tuple[float, float]:
         return lb_batch_phi_overlap(self.h, slot)
+
+    def set_layout(self, layout: int, rows_per_item: int = 1 << 30):
+        """Work-list layout (0 contiguous, 1 packed, 2 waves) and longest piece."""
+        lb_batch_set_layout(self.h, layout, rows_per_item)
+        return self
 
     def autotune(self, steps_per_candidate: int = 4) -> tuple[int, int]:
         """(layout, longest piece in rows) chosen by the library's autotuner."""

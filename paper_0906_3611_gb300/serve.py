@@ -57,12 +57,17 @@ class Result:
 
 
 class Server:
-    """Admission by HBM budget, one resident batch, chunked stepping."""
+    """Admission by HBM budget, one resident batch, chunked stepping.
+
+    The replicas change too often to autotune the batch's work list, so it is
+    fixed: `layout` = (layout, longest piece) of lb_batch_set_layout, by
+    default contiguous for the 16-bit storages and waves of 256-row pieces
+    for FP32 (the faster of the two for each on the serving workload)."""
 
     def __init__(self, phys: dict, storage: int = lb.LB_F32, capacity: int = 64,
                  budget_bytes: float = 150e9, chunk: int = 256, rho_ref=(0.88, 0.44),
                  init_kind: int = lb.LB_INIT_BERNOULLI, init=(0.7, 1.2, 0.1, 0.02),
-                 keep_state: bool = False, stream=None, batch=None):
+                 keep_state: bool = False, stream=None, batch=None, layout=None):
         self.phys = phys
         self.storage = storage
         self.capacity = capacity
@@ -77,6 +82,10 @@ class Server:
             self.stream = stream if stream is not None else torch.cuda.Stream()
             batch = lb.Batch(capacity, storage, self.stream)
         self.batch = batch
+        if layout is None:  # measured on 48 Poisson requests of 64..2048 sites a side
+            layout = (0, 1 << 30) if storage in (lb.LB_BF16_DEV, lb.LB_F16_DEV) else (2, 256)
+        if hasattr(self.batch, "set_layout"):
+            self.batch.set_layout(*layout)
         self.queue: collections.deque[Request] = collections.deque()
         self.active: dict[int, tuple[Request, float]] = {}  # slot -> (request, admitted)
         self.used = 0.0
