@@ -153,3 +153,23 @@ def test_set_state_of_a_replica_mid_run(lb, monkeypatch, storage):
     assert np.array_equal(lat.get_state(), got)
     lat.close()
     assert np.array_equal(_alone(lb, monkeypatch, 64, 24, q, 2, 25), other)
+
+
+@pytest.mark.parametrize("layout,rows", [(0, 1 << 30), (0, 7), (1, 1 << 30), (1, 33), (2, 1 << 30),
+                                         (2, 256), (2, 5)])
+def test_every_work_list_layout_keeps_results_exact(lb, monkeypatch, layout, rows):
+    """Each layout (contiguous, packed, waves) and piece length, including
+    pieces shorter than the stencil reach, gives each replica the result of
+    the lattice run alone."""
+    b = lb.Batch(8, lb.LB_F32)
+    b.set_layout(layout, rows)
+    slots = [b.add(nx, ny, _p(lb, ph, lb.LB_F32, bd, U), seed, steps)
+             for nx, ny, ph, bd, U, seed, steps in REPLICAS]
+    b.run(20)
+    assert b.status() == lb.LB_OK
+    for k, (nx, ny, ph, bd, U, seed, steps) in zip(slots, REPLICAS):
+        ref = _alone(lb, monkeypatch, nx, ny, _p(lb, ph, lb.LB_F32, bd, U), seed, min(steps, 20))
+        assert np.array_equal(b.get_state(k), ref), (nx, ny)
+    b.close()
+    with pytest.raises(lb.LBError):
+        lb.Batch(2, lb.LB_F32).set_layout(3, 64)
