@@ -66,3 +66,29 @@ def test_state_bytes_and_validation_without_gpu(lib):
     assert lib.lb_step(None, 1) == lb.LB_EINVAL
     assert lb.lb_strerror(lb.LB_ENOMEM) == "out of memory"
     assert lb.lb_time(0) == -1
+
+
+def test_invalid_arguments_of_the_newer_calls_without_gpu(lib):
+    """NULL handles and out-of-range arguments are refused before any device
+    work (shear, response record, bursts, overlap, batch layout and state)."""
+    from paper_0906_3611_gb300 import lb
+    E = lb.LB_EINVAL
+    d = ctypes.c_double()
+    n = ctypes.c_int64()
+    hist = (ctypes.c_int64 * 4)()
+    assert lib.lb_shear_diagnostics(None, ctypes.byref(d), ctypes.byref(d)) == E
+    assert lib.lb_series_start(None, 16) == E
+    assert lib.lb_series_read(None, ctypes.byref(d), 1, ctypes.byref(n)) == E
+    assert lib.lb_series_stop(None) == E
+    assert lib.lb_series_bursts(None, ctypes.c_double(2.0), 4, hist, ctypes.byref(n)) == E
+    assert lib.lb_phi_snapshot(None) == E
+    assert lib.lb_phi_overlap(None, ctypes.byref(d), ctypes.byref(d)) == E
+    assert lib.lb_batch_set_layout(None, 0, 1) == E
+    assert lib.lb_batch_set_state(None, 0, ctypes.byref(d)) == E
+    assert lib.lb_batch_series_start(None, 0, 16) == E
+    assert lib.lb_batch_series_read(None, 0, ctypes.byref(d), 1, ctypes.byref(n)) == E
+    assert lib.lb_batch_series_stop(None, 0) == E
+    assert lib.lb_batch_series_bursts(None, 0, ctypes.c_double(2.0), 4, hist, ctypes.byref(n)) == E
+    h = ctypes.c_void_p()
+    for bad in (lb.make_params(g_kolmo=1e-3, k_kolmo=0), lb.make_params(g_kolmo=float("nan"))):
+        assert lib.lb_create(64, 64, ctypes.byref(bad), None, ctypes.byref(h)) == E

@@ -173,3 +173,26 @@ def test_every_work_list_layout_keeps_results_exact(lb, monkeypatch, layout, row
     b.close()
     with pytest.raises(lb.LBError):
         lb.Batch(2, lb.LB_F32).set_layout(3, 64)
+
+
+def test_empty_and_spent_batches_run_as_no_ops(lb, monkeypatch):
+    """A batch with no replicas, with every budget spent, or emptied by
+    remove runs without error and leaves states untouched."""
+    b = lb.Batch(3, lb.LB_F32)
+    b.run(20)  # no replicas at all
+    assert b.status() == lb.LB_OK
+    p = _p(lb, CFG, lb.LB_F32, 0, 0.0)
+    k = b.add(128, 32, p, 3, 0)  # no budget
+    before = b.get_state(k)
+    b.run(17)
+    rem, done = b.poll()
+    assert rem[k] == 0 and done[k] == 0
+    assert np.array_equal(b.get_state(k), before)
+    b.set_steps(k, 4)
+    b.run(17)
+    assert b.poll()[1][k] == 4
+    assert np.array_equal(b.get_state(k), _alone(lb, monkeypatch, 128, 32, p, 3, 4))
+    b.remove(k)
+    b.run(16)
+    assert b.status() == lb.LB_OK
+    b.close()
