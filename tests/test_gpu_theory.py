@@ -10,6 +10,9 @@ pinned to (the paper states the agreement only qualitatively):
 * Laplace law (Sec. V): droplets of three radii give the same Delta p R
   (within 10 %), equal to sigma of a flat interface from (sigmaAB) with its
   tau terms (within 15 %, as the oracle) and far from it without them;
+* surface tension against tau (Sec. V, Fig. 5): flat interfaces and droplets
+  at three relaxation times as batched launches, equal to the FP64 oracle's,
+  with Delta p R following sigma with its tau terms and not the bare sigma;
 * vanishing surface tension (Sec. V.B, Fig. 7): a batch of flat interfaces,
   one physics set per rho0, gives the oracle's sigma(rho0) and a crossover
   within 0.02 of the paper's simulated 0.717 and of the theory's 0.7196.
@@ -156,3 +159,68 @@ def test_surface_tension_crossover_batched_fig7(lb):
     assert abs(xc - c["crossover_rho0_caption"]) < 0.025
     f6 = GOLD["fig6_effective"]
     assert abs(xc - T.sigma_AB_crossover(f6["mean_rho"], f6["G_AB"], f6["G_A2"], f6["G_B2"])) < 0.02
+
+
+def test_surface_tension_vs_tau_fig5_batched(lb):
+    """Fig. 5 on the GPU: flat interfaces and droplets at three relaxation
+    times (fixed rho_g^(tau) = 0.91, pure repulsion), each set run as one
+    batched launch per step with one physics set per tau, FP32.  Each sigma
+    and Delta p R equals the FP64 oracle's of the same set-up (1 %), Delta p R
+    follows sigma with its tau terms (15 %) and not the bare sigma."""
+    rg, mean, taus = GOLD["fig5_rho_g"]["rho_g"], 2.5, (0.7, 1.0, 1.5)
+    w9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+    def phys(tau):
+        return dict(tau=(tau, tau), rho0=1.0, G_AB=T.theta(tau) / rg, Ga=(0.0, 0.0),
+                    Gr=(0.0, 0.0))
+
+    x = np.arange(64)
+    rA = np.where((x >= 16) & (x < 48), 0.8 * mean, 0.2 * mean)
+    flat = np.stack([np.tile(rA, (8, 1)), np.tile(mean - rA, (8, 1))])[:, None] * w9[None, :, None, None]
+    yy, xx = np.mgrid[0:64, 0:64]
+    d = np.sqrt((xx - 31.5) ** 2 + (yy - 31.5) ** 2)
+    rD = np.where(d < 16, 0.8 * mean, 0.2 * mean)
+    drop = np.stack([rD, mean - rD])[:, None] * w9[None, :, None, None]
+
+    def run(states, shape, steps):
+        b = lb.Batch(len(taus), lb.LB_F32)
+        slots = []
+        for tau in taus:
+            p = lb.make_params(**phys(tau), storage=lb.LB_F32, rho_ref=(mean / 2, mean / 2))
+            slots.append(b.add(shape[1], shape[0], p, 0, steps))
+            b.set_state(slots[-1], states)
+        b.run(steps)
+        assert b.status() == lb.LB_OK
+        out = [b.observables(s, fields=True)["rho"] for s in slots]
+        b.close()
+        return out
+
+    def laplace(rd, g):
+        ain, aout = rd[0, 32, 32], rd[0, 2, 2]
+        R = math.sqrt(((rd[0] - aout) / (ain - aout)).sum() / math.pi)
+        dp = (T.bulk_pressure(rd[0, 32, 32], rd[1, 32, 32], g, 0, 0, 1.0)
+              - T.bulk_pressure(rd[0, 2, 2], rd[1, 2, 2], g, 0, 0, 1.0))
+        return dp * R
+
+    def sigmas(r, tau, g):
+        return [T.sigma_flat_profile(r[0, 2], r[1, 2], tau, g, 0.0, 0.0, 1.0, slice(0, 32), tt)
+                for tt in (True, False)]
+
+    flats, drops = run(flat, (8, 64), 20000), run(drop, (64, 64), 8000)
+    bare_err = []
+    for tau, rf, rd in zip(taus, flats, drops):
+        g = T.theta(tau) / rg
+        st, sb = sigmas(rf, tau, g)
+        lap = laplace(rd, g)
+        # the FP64 oracle on the same set-up
+        of, _ = oracle.step(flat[:, :, :4], phys(tau), 20000)
+        od, _ = oracle.step(drop, phys(tau), 8000)
+        ost, osb = sigmas(oracle.densities(of), tau, g)
+        olap = laplace(oracle.densities(od), g)
+        print("tau", tau, "sigma_tau", st, ost, "bare", sb, osb, "laplace", lap, olap)
+        assert st == pytest.approx(ost, rel=1e-2) and sb == pytest.approx(osb, rel=1e-2)
+        assert lap == pytest.approx(olap, rel=1e-2)
+        assert lap == pytest.approx(st, rel=0.15)
+        assert abs(lap - st) < abs(lap - sb)
+        bare_err.append(abs(lap / sb - 1.0))
+    assert bare_err[0] < bare_err[1] < bare_err[2]

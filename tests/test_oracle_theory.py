@@ -5,7 +5,8 @@ with the closed forms / root-finders of oracle/theory.py:
 * pure repulsion: the zero-diffusion manifold rho_A/rho_B = exp((rho_A-rho_B)/rho_g^(tau))
   (Eq. (RHOGTAU), system (FIXING)) and the bulk densities (Sec. IV.A, Fig. 3);
 * self-interactions: the symmetric bulk free energy (BULKfinal) (Sec. IV.C, Fig. 4);
-* Laplace law P_in - P_out = sigma/R against sigma of (sigmaAB) with its tau terms (Sec. V);
+* Laplace law P_in - P_out = sigma/R against sigma of (sigmaAB) with its tau terms,
+  across tau at fixed rho_g^(tau) (Sec. V, Fig. 5);
 * the vanishing-surface-tension crossover of Eq. (surften) (Fig. 6), and the
   simulated one of Fig. 7: sigma of (sigmaAB), with its tau terms, on
   equilibrated flat interfaces changes sign near the paper's rho0 = 0.717.
@@ -95,30 +96,47 @@ def test_self_interaction_config_couplings():
 
 
 @pytest.mark.slow
-def test_laplace_law_needs_the_tau_corrections():
-    """Delta p R of a droplet against sigma of a flat interface, Eq. (sigmaAB)."""
-    tau = 1.0
+def laplace_and_flat_sigma(tau, mean=2.5, n=64, R0=16, flat_steps=20000, drop_steps=8000):
+    """Fig. 5 set-up (pure repulsion at fixed rho_g^(tau)): sigma of (sigmaAB) of a
+    flat interface with and without its tau terms, and Delta p R of a droplet."""
     rg = GOLD["fig5_rho_g"]["rho_g"]
     g = T.theta(tau) / rg
-    mean = 2.5
     p = dict(tau=(tau, tau), rho0=1.0, G_AB=g)
-    r = _flat_interface(mean, p)
+    r = _flat_interface(mean, p, nx=64, ny=4, steps=flat_steps)
     sig_tau = T.sigma_flat_profile(r[0, 2], r[1, 2], tau, g, 0.0, 0.0, 1.0, slice(0, 32), True)
     sig_bare = T.sigma_flat_profile(r[0, 2], r[1, 2], tau, g, 0.0, 0.0, 1.0, slice(0, 32), False)
-    n, R0 = 64, 16
     yy, xx = np.mgrid[0:n, 0:n]
     d = np.sqrt((xx - n / 2 + 0.5) ** 2 + (yy - n / 2 + 0.5) ** 2)
     rA = np.where(d < R0, 0.8 * mean, 0.2 * mean)
     f = np.stack([rA, mean - rA])[:, None] * W9[None, :, None, None]
-    gd, _ = oracle.step(f, p, 8000)
+    gd, _ = oracle.step(f, p, drop_steps)
     rd = oracle.densities(gd)
+    return sig_tau, sig_bare, laplace_of(rd, g)
+
+
+def laplace_of(rd, g):
+    """Delta p R of an equilibrated droplet: bulk pressures (PBULKINT) at the
+    centre and in a corner, R from the A excess."""
+    n = rd.shape[1]
     ain, aout = rd[0, n // 2, n // 2], rd[0, 2, 2]
     R = math.sqrt(((rd[0] - aout) / (ain - aout)).sum() / math.pi)
     dp = (T.bulk_pressure(rd[0, n // 2, n // 2], rd[1, n // 2, n // 2], g, 0, 0, 1.0)
           - T.bulk_pressure(rd[0, 2, 2], rd[1, 2, 2], g, 0, 0, 1.0))
-    lap = dp * R
-    assert lap == pytest.approx(sig_tau, rel=0.15)
-    assert abs(lap - sig_tau) < 0.25 * abs(lap - sig_bare)
+    return dp * R
+
+
+def test_laplace_law_needs_the_tau_corrections_fig5():
+    """Fig. 5: at fixed rho_g^(tau) = 0.91, Delta p R of droplets follows sigma
+    of (sigmaAB) with its tau terms (within 15 %, as at tau = 1) for every tau,
+    while the bare sigma falls ever further behind as tau grows."""
+    bare_err = []
+    for tau in (0.7, 1.0, 1.5):
+        sig_tau, sig_bare, lap = laplace_and_flat_sigma(tau)
+        assert lap == pytest.approx(sig_tau, rel=0.15), tau
+        assert abs(lap - sig_tau) < abs(lap - sig_bare), tau
+        bare_err.append(abs(lap / sig_bare - 1.0))
+    assert bare_err[0] < bare_err[1] < bare_err[2]
+    assert bare_err[2] > 1.0  # at tau = 1.5 the bare sigma is off by more than 100 %
 
 
 def test_effective_couplings_reproduce_printed_values():
