@@ -487,6 +487,15 @@ def run_shear(args):
     Kt = np.mean(series ** 4, axis=0) / np.mean(series ** 2, axis=0) ** 2
     hist = np.sum([x["hist"] for x in bursts], axis=0)
     events = int(sum(x["events"] for x in bursts))
+    # exponent of the burst-wait pdf (Fig. 14): least-squares slope of the
+    # log-binned density over the bins holding at least 5 waits
+    dens = hist / 2.0 ** np.arange(nb)
+    used = hist >= 5
+    alpha = (float(-np.polyfit(np.arange(nb)[used] + np.log2(1.5), np.log2(dens[used]), 1)[0])
+             if used.sum() >= 3 else None)
+    # R at three close late times over the ensemble (Fig. 17)
+    late = series[:, -3:].ravel()
+    late_sd = float(late.std())
     C = D.sum(sum(o[0] for o in ov)) / D.sum(sum(o[1] for o in ov))
     R = np.array(D.gather([d["U_k"] / U0 for d in diag]))
     iab = np.array(D.gather([d["I_AB"] for d in diag]))
@@ -520,7 +529,12 @@ def run_shear(args):
                                             "final": float(Kt[-1]), "mean": float(Kt.mean()),
                                             "max": float(Kt.max())},
                              "bursts": {"c_sigma": 3.0, "events": events,
-                                        "wait_hist_log2": [int(v) for v in hist]}},
+                                        "wait_hist_log2": [int(v) for v in hist],
+                                        "alpha_logbinned": alpha},
+                             "R_late": {"samples": int(late.size), "mean": float(late.mean()),
+                                        "sd": late_sd,
+                                        "skew": float(np.mean((late - late.mean()) ** 3))
+                                        / late_sd ** 3 if late_sd > 0 else None}},
                 "gpu_launches": args.steps, "clocks": clocks,
                 "status": lb.lb_strerror(status), "impl": "gb300"}
         print(json.dumps(line), flush=True)
