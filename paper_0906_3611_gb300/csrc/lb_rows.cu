@@ -34,6 +34,8 @@ __global__ void __launch_bounds__(cta_threads<STORAGE>(), RowsCfg<STORAGE>::MINB
     s_abort = 0;
   }
   __syncthreads();
+  wait_previous_grid();
+  allow_next_grid();
   int ring = 0, bad = 0;
   const Series none{};
   rows_range<STORAGE, (MODE > 0)>(src, dst, g, ph, ph.Uwall, body, x0, x1, ylo, yhi, sm, ring,
@@ -136,16 +138,17 @@ static cudaError_t rows_t(const void* src, void* dst, const Geom& g, const PhysD
   sr.expected = (unsigned)(nstrips * k * RowsCfg<STORAGE>::NCW);  // every compute warp, once
   const Phys<C> ph = make_phys<C>(pd);
   const int nb = nstrips * k, th = cta_threads<STORAGE>();
+  const T2* s2 = (const T2*)src;
+  T2* d2 = (T2*)dst;
+  const bool dep = (long long)g.nx * g.ny < kDependentLaunchSites;
   if (sr.buf)
-    k_rows<STORAGE, 2><<<nb, th, smem, st>>>((const T2*)src, (T2*)dst, g, ph, body, nstrips, k,
-                                            status, sr);
-  else if (body)
-    k_rows<STORAGE, 1><<<nb, th, smem, st>>>((const T2*)src, (T2*)dst, g, ph, body, nstrips, k,
-                                            status, sr);
-  else
-    k_rows<STORAGE, 0><<<nb, th, smem, st>>>((const T2*)src, (T2*)dst, g, ph, body, nstrips, k,
-                                            status, sr);
-  return cudaGetLastError();
+    return launch_step_kernel(dep, k_rows<STORAGE, 2>, nb, th, smem, st, s2, d2, g, ph, body,
+                              nstrips, k, status, sr);
+  if (body)
+    return launch_step_kernel(dep, k_rows<STORAGE, 1>, nb, th, smem, st, s2, d2, g, ph, body,
+                              nstrips, k, status, sr);
+  return launch_step_kernel(dep, k_rows<STORAGE, 0>, nb, th, smem, st, s2, d2, g, ph, body,
+                            nstrips, k, status, sr);
 }
 
 cudaError_t launch_step_rows(int storage, const void* src, void* dst, const Geom& g,

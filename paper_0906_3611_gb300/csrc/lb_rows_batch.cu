@@ -40,6 +40,8 @@ __global__ void __launch_bounds__(cta_threads<STORAGE>(), RowsCfg<STORAGE>::MINB
     sm.init();
     s_abort = 0;
   }
+  wait_previous_grid();  // (before the first global access: the records, the work list)
+  allow_next_grid();
   int ring = 0, bad = 0;
   const int it1 = offsets[blockIdx.x + 1];
   for (int it = offsets[blockIdx.x]; it < it1; ++it) {
@@ -126,13 +128,15 @@ static cudaError_t rows_batch_v(void* reps, const WorkItem* items, const int* of
   const PhysTable<C>& tab = *(const PhysTable<C>*)table;
   const int th = cta_threads<STORAGE>();
   const size_t smem = rows_smem_bytes<STORAGE>();
+  // (an ordinary launch: the batched step is long, see launch_step_kernel)
   if (mode == 2)
-    k_rows_batch<STORAGE, ONE, 2><<<grid, th, smem, st>>>(R, items, offsets, status, tab);
-  else if (mode == 1)
-    k_rows_batch<STORAGE, ONE, 1><<<grid, th, smem, st>>>(R, items, offsets, status, tab);
-  else
-    k_rows_batch<STORAGE, ONE, 0><<<grid, th, smem, st>>>(R, items, offsets, status, tab);
-  return cudaGetLastError();
+    return launch_step_kernel(false, k_rows_batch<STORAGE, ONE, 2>, grid, th, smem, st, R, items,
+                              offsets, status, tab);
+  if (mode == 1)
+    return launch_step_kernel(false, k_rows_batch<STORAGE, ONE, 1>, grid, th, smem, st, R, items,
+                              offsets, status, tab);
+  return launch_step_kernel(false, k_rows_batch<STORAGE, ONE, 0>, grid, th, smem, st, R, items,
+                            offsets, status, tab);
 }
 
 template <int STORAGE>
