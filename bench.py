@@ -128,6 +128,100 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+class NvmlClocks:
+    """In-process NVML samples of the SM clock, power and clock-event reasons,
+    taken every ~10 ms on a background thread (libnvidia-ml through ctypes;
+    reads only).  Samples taken while `loaded` is set (the timed region) are the
+    under-load samples.  Falls back to the nvidia-smi sampler without NVML."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, local: int, period_s: float = 0.01):
+        import ctypes
+        import threading
+        self.period = period_s
+        self.samples = []  # (loaded, sm_mhz, power_w, reasons bitmask)
+        self.loaded = False
+        self.fallback = None
+        self._stop = threading.Event()
+        self._thread = None
+        self.lib = None
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                raise OSError("nvmlInit")
+            h = ctypes.c_void_p()
+            ok = False
+            try:
+                import torch
+                pr = torch.cuda.get_device_properties(local)
+                bus = "%08x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+                ok = lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(h)) == 0
+            except Exception:
+                ok = False
+            if not ok:
+                vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+                idx = int(vis.split(",")[local]) if vis and vis.split(",")[0].isdigit() else local
+                if lib.nvmlDeviceGetHandleByIndex_v2(idx, ctypes.byref(h)) != 0:
+                    raise OSError("nvmlDeviceGetHandle")
+            self.h = h
+            self.lib = lib
+            self.ct = ctypes
+            self.reason_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                lib.nvmlDeviceGetCurrentClocksThrottleReasons
+            mx = ctypes.c_uint()
+            lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))  # NVML_CLOCK_SM
+            self.max_mhz = float(mx.value)
+        except Exception:
+            self.lib = None
+            self.fallback = ClockSampler(local)
+
+    def _sample(self):
+        ct = self.ct
+        mhz, mw, rs = ct.c_uint(), ct.c_uint(), ct.c_ulonglong()
+        self.lib.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(mhz))
+        self.lib.nvmlDeviceGetPowerUsage(self.h, ct.byref(mw))
+        self.reason_fn(self.h, ct.byref(rs))
+        self.samples.append((self.loaded, float(mhz.value), mw.value / 1e3, int(rs.value)))
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                self._sample()
+            except Exception:
+                pass
+            time.sleep(self.period)
+
+    def start(self):
+        if self.fallback is not None:
+            self.fallback.start()
+            return
+        import threading
+        self._thread = threading.Thread(target=self._run, daemon=True)
+        self._thread.start()
+
+    def stop(self) -> dict:
+        if self.fallback is not None:
+            return self.fallback.stop()
+        self._stop.set()
+        self._thread.join(timeout=2)
+        load = [x for x in self.samples if x[0]]
+        use = load or self.samples
+        if not use:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["no samples"],
+                    "samples": 0, "samples_under_load": 0, "source": "nvml"}
+        reasons = set()
+        for x in use:
+            for bit, nm in self.REASONS.items():
+                if x[3] & bit:
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(x[1] for x in use), "sm_max_mhz": self.max_mhz,
+                "sm_mhz_min": min(x[1] for x in use), "power_w_max": max(x[2] for x in use),
+                "reasons": sorted(reasons), "samples": len(self.samples),
+                "samples_under_load": len(load), "source": "nvml, 10 ms"}
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -236,6 +330,67 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def timed_blocks(D, stream, fn, reps, clocks=None, target_s=None):
+    """Time blocks of work: each block is fn() (K steps enqueued on `stream`),
+    bracketed by a barrier and a device synchronize, timed with CUDA events on
+    that stream; a block's time is the max over ranks.  With `target_s` the
+    repetition count grows from `reps` until about that many seconds are
+    timed.  Returns the list of block times (ms)."""
+    import torch
+
+    out = []
+    r = 0
+    while True:
+        D.barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        if clocks is not None:
+            clocks.loaded = True
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        if clocks is not None:
+            clocks.loaded = False
+        D.barrier()
+        out.append(D.max(a.elapsed_time(b)))
+        r += 1
+        if r == 1 and target_s:  # size the run from the first block
+            reps = int(D.max(max(reps, min(4000, int(target_s * 1e3 / max(out[0], 1e-3))))))
+        if r >= reps:
+            return out
+
+
+def lattice_params(lb, storage, boundary, U):
+    return lb.make_params(**PHYS, boundary=boundary, U_wall=U, storage=storage,
+                          rho_ref=(0.87, 0.43), init_kind=lb.LB_INIT_BERNOULLI, init=INIT)
+
+
+def single_lattice(lb, D, name, steps, warmup, seed, reps=25, target_s=1.5, clocks=None, U=None):
+    """MLUPS of one lattice workload: the median over repeated blocks of `steps`
+    graph-replayed steps.  Returns (dict, lattice, stream)."""
+    import torch
+
+    nx, ny, boundary, U0, storage = WORKLOADS[name]
+    U = U0 if U is None else U
+    stream = torch.cuda.Stream()
+    lat = lb.Lattice(nx, ny, lattice_params(lb, storage, boundary, U), stream=stream)
+    lat.init_random(seed)
+    lat.step(warmup)
+    lat.sync()
+    ms = timed_blocks(D, stream, lambda: lat.step(steps), reps, clocks, target_s)
+    med = statistics.median(ms)
+    bps = 2 * 18 * ELEM[storage]  # 18 populations read + 18 written per site
+    peak, peak_kind = peaks()
+    achieved = bps * nx * ny / (med * 1e-3 / steps) / 1e9
+    out = {"workload": name, "mlups": whole_job_mlups(D.sum(nx * ny * steps), med * 1e-3),
+           "ms_per_step": med / steps, "blocks": len(ms), "steps_per_block": steps,
+           "ms_block_min_max": [min(ms), max(ms)], "bytes_per_site": bps,
+           "achieved_gbs": achieved, "frac": achieved / peak, "peak_gbs": peak,
+           "peak_kind": peak_kind, "status": lb.lb_strerror(lat.status())}
+    return out, lat, stream
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -246,32 +401,14 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     D = Dist()
     nx, ny, boundary, U, storage = WORKLOADS[args.workload]
-    params = lb.make_params(**PHYS, boundary=boundary, U_wall=U, storage=storage,
-                            rho_ref=(0.87, 0.43), init_kind=lb.LB_INIT_BERNOULLI, init=INIT)
-    stream = torch.cuda.Stream()
-    lat = lb.Lattice(nx, ny, params, stream=stream)
-    lat.init_random(rank)
     sites = nx * ny
-
-    barrier = D.barrier
-
-    sampler = ClockSampler(torch.cuda.current_device() if world == 1 else local)
-    sampler.start()
-    lat.step(args.warmup)
-    lat.sync()
-    barrier()
-    start = torch.cuda.Event(enable_timing=True)
-    end = torch.cuda.Event(enable_timing=True)
-    start.record(stream)
-    lat.step(args.steps)
-    end.record(stream)
-    end.synchronize()
-    barrier()
-    clocks = sampler.stop()
-    ms = start.elapsed_time(end)
-    status = lat.status()
-    ms_max = D.max(ms)
-    value = whole_job_mlups(D.sum(sites * args.steps), ms_max * 1e-3)
+    clocks = NvmlClocks(local)
+    clocks.start()
+    res, lat, stream = single_lattice(lb, D, args.workload, args.steps, args.warmup, rank,
+                                      reps=args.reps, target_s=args.target_s, clocks=clocks)
+    clocks_d = clocks.stop()
+    ms = res["ms_per_step"] * args.steps  # median block time, max over ranks
+    value = res["mlups"]
 
     # end-to-end through the C ABI with host buffers: pinned host state -> device,
     # K steps, FP64 observables back to the host
@@ -280,27 +417,45 @@ def run_gpu(args):
     lb.lb_get_state_raw(lat.h, host.data_ptr())
     mass = np.zeros(4)
     stress = np.zeros(3)
-    barrier()
-    t0 = time.perf_counter()
-    lb.lb_set_state_raw(lat.h, host.data_ptr())
-    lb.lb_step(lat.h, args.steps)
-    lb.lb_observables(lat.h, None, None, stress, mass)
-    e2e_s = time.perf_counter() - t0
-    e2e_value = whole_job_mlups(D.sum(sites * args.steps), D.max(e2e_s))
+    e2e = []
+    for _ in range(3):
+        D.barrier()
+        t0 = time.perf_counter()
+        lb.lb_set_state_raw(lat.h, host.data_ptr())
+        lb.lb_step(lat.h, args.steps)
+        lb.lb_observables(lat.h, None, None, stress, mass)
+        e2e.append(D.max(time.perf_counter() - t0))
+    e2e_value = whole_job_mlups(D.sum(sites * args.steps), statistics.median(e2e))
+    status = lat.status()
+    lat.close()
 
-    bytes_per_site = 2 * 18 * es  # 18 populations read + 18 written
-    kernel_s = ms * 1e-3 / args.steps
-    achieved = bytes_per_site * sites / kernel_s / 1e9
-    peak, peak_kind = peaks()
+    bytes_per_site = res["bytes_per_site"]
+    achieved = res["achieved_gbs"]
+    peak, peak_kind = res["peak_gbs"], res["peak_kind"]
     traffic = None
+    tr = {}
     prof = os.path.join(ROOT, "profiles", "traffic.txt")
     if os.path.exists(prof):
+        from paper_0906_3611_gb300 import build as _b
+        sha = _b.kernel_sha()
         for line in open(prof):
             if line.startswith(f"{args.workload} ") and "kernel_sha=" in line:
                 parts = dict(kv.split("=", 1) for kv in line.split()[1:] if "=" in kv)
-                from paper_0906_3611_gb300 import build as _b
-                if parts.get("kernel_sha") == _b.kernel_sha():
-                    traffic = float(parts["bytes_per_launch"])
+                if parts.get("kernel_sha") == sha:
+                    tr = parts
+                    traffic = float(parts["read_bytes"]) + float(parts["write_bytes"])
+
+    extra = None
+    if world == 1 and not args.no_extra and args.workload == "couette4096_f32":
+        # the reduced-storage forms on the same GPU, against this line's FP32 lattice
+        f16, l16, _ = single_lattice(lb, D, "couette4096_f16dev", args.steps, args.warmup, 0,
+                                     reps=args.reps, target_s=args.target_s)
+        l16.close()
+        b16 = batch_measure(lb, D, "batch256_f16dev", args.steps, args.warmup, reps=5,
+                            target_s=args.target_s)
+        extra = {"couette4096_f16dev": f16, "batch256_f16dev": b16,
+                 "batched_f16dev_over_f32_single": b16["mlups"] / value,
+                 "single_f16dev_over_f32_single": f16["mlups"] / value}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -310,28 +465,87 @@ def run_gpu(args):
                "sample": f"FP64 oracle, full {nx}x{ny} lattice of this workload, {cs} steps "
                          f"({dt_cpu:.1f} s), OpenMP {cores} threads"}
     if rank == 0:
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "bytes_per_site": bytes_per_site,
+                "peak_kind": peak_kind}
+        if tr:
+            roof["traffic_read"] = float(tr["read_bytes"])
+            roof["traffic_write"] = float(tr["write_bytes"])
+            roof["read_amplification"] = float(tr["read_bytes"]) / (bytes_per_site / 2 * sites)
+            roof["traffic_source"] = tr.get("source")
         line = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if storage != 0 else "f64", "data": "synthetic",
                 "config": {"workload": args.workload, "nx": nx, "ny": ny,
                            "boundary": "couette" if boundary else "periodic", "U_wall": U,
                            "storage": STORAGE_NAME[storage], "init": "bernoulli(0.7) droplets",
                            "l2": f"inputs larger than L2 ({lb.lb_state_bytes(nx, ny, storage) / 1e9:.2f} GB per buffer)",
+                           "timing": f"median of {res['blocks']} timed blocks of {args.steps} "
+                                     "graph-replayed steps, each between barriers",
                            "parallelism": f"replicas{world}"},
-                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "traffic": traffic,
-                             "bytes_per_site": bytes_per_site, "peak_kind": peak_kind},
+                "roofline": roof,
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": "MLUPS",
                         "h2d_bytes_per_step": 18 * 2 * sites * es / args.steps,
                         "d2h_bytes_per_step": 7 * 8 / args.steps},
-                "gpu_launches": args.steps,
-                "clocks": clocks,
+                "gpu_launches": args.steps * res["blocks"],
+                "clocks": clocks_d,
+                "reduced_storage": extra,
                 "status": lb.lb_strerror(status),
                 "impl": "gb300"}
         print(json.dumps(line), flush=True)
-    lat.close()
+    D.close()
+
+
+def run_sweep(args):
+    """C3 at the Couette workload's size: every storage and wall speed, MLUPS and
+    the FP64 stresses (mean sigma_xy, both walls) averaged over the second half
+    of the run (sampled every `--sample-every` steps)."""
+    import numpy as np
+    import torch
+
+    from paper_0906_3611_gb300 import lb
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    D = Dist()
+    rows = []
+    every = max(1, args.sample_every)
+    for name in ("couette4096_f32", "couette4096_f16dev", "couette4096_bf16dev"):
+        nx, ny, boundary, _, storage = WORKLOADS[name]
+        for U in (0.005, 0.02, 0.05):
+            stream = torch.cuda.Stream()
+            lat = lb.Lattice(nx, ny, lattice_params(lb, storage, boundary, U), stream=stream)
+            lat.init_random(rank)
+            lat.step(args.warmup)
+            lat.sync()
+            ms_total, acc, n_acc, t = 0.0, np.zeros(3), 0, 0
+            while t < args.steps:
+                k = min(every, args.steps - t)
+                ms_total += timed_blocks(D, stream, lambda: lat.step(k), 1)[0]
+                t += k
+                if t > args.steps // 2:
+                    acc += lat.observables()["stress"]
+                    n_acc += 1
+            st = lat.status()
+            ob = lat.observables()
+            lat.close()
+            rows.append({"workload": name, "storage": STORAGE_NAME[storage], "U": U,
+                         "mlups": whole_job_mlups(D.sum(nx * ny * args.steps), ms_total * 1e-3),
+                         "stress_mean_second_half": (acc / max(n_acc, 1)).tolist(),
+                         "stress_final": ob["stress"].tolist(), "mass_final": ob["mass"].tolist(),
+                         "status": lb.lb_strerror(st)})
+    if rank == 0:
+        line = {"metric": "MLUPS", "value": statistics.median(r["mlups"] for r in rows),
+                "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": "couette4096_sweep", "nx": 4096, "ny": 4096,
+                           "U_wall": [0.005, 0.02, 0.05], "storages": ["f32", "f16dev", "bf16dev"],
+                           "stress": "[mean sigma_xy, wall_top, wall_bottom], FP64 reductions"},
+                "sweep": rows, "impl": "gb300"}
+        print(json.dumps(line), flush=True)
     D.close()
 
 
@@ -346,56 +560,37 @@ def batch_replicas(name):
     return [(int(side[k]), float(U[k]), k) for k in range(n)], storage
 
 
-def run_batch(args):
-    """Batched ensemble: all replicas in one persistent launch per step, against
-    the same replicas stepped one lattice at a time (sequential launches)."""
+def batch_measure(lb, D, name, steps, warmup, reps=5, target_s=None, clocks=None):
+    """A batched ensemble: all replicas in one persistent launch per step (the
+    median over repeated blocks of `steps` graph-replayed launches), against the
+    same replicas stepped one lattice at a time (sequential launches)."""
     import torch
 
-    from paper_0906_3611_gb300 import lb
-
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    D = Dist()
-    reps, storage = batch_replicas(args.workload)
+    reps_list, storage = batch_replicas(name)
     stream = torch.cuda.Stream()
 
     def prm(U):
         return lb.make_params(**PHYS, boundary=lb.LB_COUETTE, U_wall=U, storage=storage,
                               rho_ref=(0.88, 0.44), init_kind=lb.LB_INIT_BERNOULLI, init=INIT)
 
-    sites = sum(side * side for side, _, _ in reps)
-    b = lb.Batch(len(reps), storage, stream)
-    budget = args.warmup + args.steps + 64
-    for side, U, seed in reps:
+    sites = sum(side * side for side, _, _ in reps_list)
+    b = lb.Batch(len(reps_list), storage, stream)
+    budget = 1 << 40  # effectively unbounded: every replica steps in every launch
+    for side, U, seed in reps_list:
         b.add(side, side, prm(U), seed, budget)
     layout, rows = b.autotune(2)
-    for k in range(len(reps)):  # the autotuner spent budget: refill it
-        b.set_steps(k, args.warmup + args.steps)
-    sampler = ClockSampler(local)
-    sampler.start()
-    b.run(args.warmup)
+    b.run(warmup)
     stream.synchronize()
-    D.barrier()
-    start = torch.cuda.Event(enable_timing=True)
-    end = torch.cuda.Event(enable_timing=True)
-    start.record(stream)
-    b.run(args.steps)
-    end.record(stream)
-    end.synchronize()
-    D.barrier()
-    clocks = sampler.stop()
-    ms = start.elapsed_time(end)
-    rem, done = b.poll()
+    ms = timed_blocks(D, stream, lambda: b.run(steps), reps, clocks, target_s)
     status = b.status()
     b.close()
-    ms_max = D.max(ms)
-    value = whole_job_mlups(D.sum(sites * args.steps), ms_max * 1e-3)
+    med = statistics.median(ms)
+    value = whole_job_mlups(D.sum(sites * steps), med * 1e-3)
 
     # the same replicas, one lattice at a time (each replica's steps in one lb_step)
-    seq_steps = max(1, args.steps // 4)
-    lats = []
+    seq_steps = max(1, steps // 4)
     t_seq = 0.0
-    for side, U, seed in reps:
+    for side, U, seed in reps_list:
         lat = lb.Lattice(side, side, prm(U), stream=stream).init_random(seed)
         lat.step(3)
         stream.synchronize()
@@ -409,27 +604,51 @@ def run_batch(args):
         lat.close()
     seq_value = whole_job_mlups(D.sum(sites * seq_steps), D.max(t_seq) * 1e-3)
     es = ELEM[storage]
-    bytes_per_site = 2 * 18 * es
-    achieved = bytes_per_site * sites / (ms * 1e-3 / args.steps) / 1e9
+    bps = 2 * 18 * es
     peak, peak_kind = peaks()
+    achieved = bps * sites / (med * 1e-3 / steps) / 1e9
+    return {"workload": name, "mlups": value, "ms_per_step": med / steps, "blocks": len(ms),
+            "steps_per_block": steps, "replicas": len(reps_list), "sites": sites,
+            "sequential_single_lattice_mlups": seq_value, "over_sequential": value / seq_value,
+            "work_list": {"layout": ["contiguous", "packed", "waves"][layout],
+                          "max_piece_rows": rows},
+            "bytes_per_site": bps, "achieved_gbs": achieved, "frac": achieved / peak,
+            "peak_gbs": peak, "peak_kind": peak_kind, "storage": STORAGE_NAME[storage],
+            "status": lb.lb_strerror(status)}
+
+
+def run_batch(args):
+    """Batched ensemble: all replicas in one persistent launch per step, against
+    the same replicas stepped one lattice at a time (sequential launches)."""
+    import torch
+
+    from paper_0906_3611_gb300 import lb
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    D = Dist()
+    clocks = NvmlClocks(local)
+    clocks.start()
+    r = batch_measure(lb, D, args.workload, args.steps, args.warmup, reps=max(3, args.reps // 5),
+                      target_s=args.target_s, clocks=clocks)
+    clocks_d = clocks.stop()
     if rank == 0:
-        line = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        line = {"metric": "MLUPS", "value": r["mlups"], "unit": "MLUPS", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic",
-                "config": {"workload": args.workload, "replicas": len(reps), "sites": sites,
-                           "sides": sorted(set(s for s, _, _ in reps)),
-                           "storage": STORAGE_NAME[storage], "boundary": "couette",
-                           "U_wall": "uniform[0, 0.05]",
-                           "work_list": {"layout": ["contiguous", "packed", "waves"][layout],
-                                         "max_piece_rows": rows},
-                           "l2": f"inputs larger than L2 ({sites * 18 * es / 1e9:.1f} GB per buffer set)"},
-                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "traffic": None,
-                             "bytes_per_site": bytes_per_site, "peak_kind": peak_kind},
-                "sequential_single_lattice_mlups": seq_value,
-                "gpu_launches": args.steps, "clocks": clocks,
-                "status": lb.lb_strerror(status), "impl": "gb300"}
+                "config": {"workload": args.workload, "replicas": r["replicas"], "sites": r["sites"],
+                           "sides": sorted(set(s for s, _, _ in batch_replicas(args.workload)[0])),
+                           "storage": r["storage"], "boundary": "couette",
+                           "U_wall": "uniform[0, 0.05]", "work_list": r["work_list"],
+                           "timing": f"median of {r['blocks']} timed blocks of {args.steps} launches",
+                           "l2": f"inputs larger than L2 ({r['sites'] * 18 * ELEM[BATCHES[args.workload][3]] / 1e9:.1f} GB per buffer set)"},
+                "roofline": {"bound": "hbm", "achieved": r["achieved_gbs"], "peak": r["peak_gbs"],
+                             "unit": "GB/s", "frac": r["frac"], "traffic": None,
+                             "bytes_per_site": r["bytes_per_site"], "peak_kind": r["peak_kind"]},
+                "sequential_single_lattice_mlups": r["sequential_single_lattice_mlups"],
+                "gpu_launches": args.steps * r["blocks"], "clocks": clocks_d,
+                "status": r["status"], "impl": "gb300"}
         print(json.dumps(line), flush=True)
     D.close()
 
@@ -458,7 +677,7 @@ def run_shear(args):
     layout, rows = b.autotune(2)
     for r in range(n):
         b.set_steps(r, args.warmup + args.steps)
-    sampler = ClockSampler(local)
+    sampler = NvmlClocks(local)
     sampler.start()
     b.run(args.warmup)
     stream.synchronize()
@@ -469,10 +688,12 @@ def run_shear(args):
     D.barrier()
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
+    sampler.loaded = True
     start.record(stream)
     b.run(args.steps)
     end.record(stream)
     end.synchronize()
+    sampler.loaded = False
     D.barrier()
     clocks = sampler.stop()
     ms = start.elapsed_time(end)
@@ -557,12 +778,14 @@ def run_serve(args):
     reqs = serve.poisson_requests(n, rate=rate, seed=rank, sides=sides, steps_range=steps_range)
     offered = sum(r.side * r.side * r.steps for r in reqs)
     srv = serve.Server(PHYS, storage, capacity=slots, chunk=chunk, budget_bytes=budget)
-    sampler = ClockSampler(local)
+    sampler = NvmlClocks(local)
     sampler.start()
     D.barrier()
     t0 = time.perf_counter()
+    sampler.loaded = True
     res = srv.run(reqs)
     torch.cuda.synchronize()
+    sampler.loaded = False
     wall = time.perf_counter() - t0
     D.barrier()
     clocks = sampler.stop()
@@ -601,15 +824,25 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="couette4096_f32",
-                    choices=sorted(WORKLOADS) + sorted(BATCHES) + sorted(SHEARS) + sorted(SERVES))
+                    choices=sorted(WORKLOADS) + sorted(BATCHES) + sorted(SHEARS) + sorted(SERVES)
+                    + ["couette4096_sweep"])
     ap.add_argument("--requests", type=int, default=0)
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the reduced-storage keys of the default line")
+    ap.add_argument("--reps", type=int, default=25, help="timed blocks of --steps steps (minimum)")
+    ap.add_argument("--target-s", type=float, default=1.5,
+                    help="grow the timed blocks to about this many seconds")
+    ap.add_argument("--sample-every", type=int, default=1000,
+                    help="couette4096_sweep: steps between stress samples")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "couette4096_sweep":
+        run_sweep(args)
     elif args.workload in BATCHES:
         run_batch(args)
     elif args.workload in SHEARS:

@@ -249,11 +249,15 @@ LB_API void lb_destroy(lb_handle *h);
  * The partial sums live in a fixed static device array of 4 MiB + 64 B that
  * every GPU loading the library holds until exit; it serves lattices of up to
  * 65536 tiles of 32 x 8 sites (e.g. 4096 x 4096), larger ones get
- * LB_ETOOBIG.  The first call on a device looks the array's device address up
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the array: calls whose work
- * overlaps on the GPU race and must be serialised by the caller.
- * Asynchronous: returns after enqueueing; allocates nothing. */
+ * LB_ETOOBIG.  The array's device address is looked up (cudaGetSymbolAddress,
+ * for the calling thread's current context) on every call made outside stream
+ * capture, so a device reset or another context on the same device is
+ * followed; a call whose stream is capturing reuses the address found for its
+ * context by an earlier uncaptured call, so make one call outside any capture
+ * first.  All calls share the array: calls whose work overlaps on the GPU
+ * race and must be serialised by the caller.  Parameters are checked like
+ * lb_create's (LB_EINVAL).  Asynchronous: returns after enqueueing; allocates
+ * nothing. */
 LB_API int lb_observables_noalloc(const void *f, int nx, int ny, int pitch, const lb_params *p,
                                   void *cuda_stream, double *out);
 

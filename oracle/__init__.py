@@ -72,6 +72,8 @@ def _load():
         lib.lbo_init_densities.restype = None
         lib.lbo_shear_diagnostics.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, dp]
         lib.lbo_shear_diagnostics.restype = ctypes.c_long
+        lib.lbo_phi_overlap.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, dp]
+        lib.lbo_phi_overlap.restype = None
         lib.lbo_max_threads.argtypes = []
         lib.lbo_max_threads.restype = ctypes.c_int
         _lib = lib
@@ -164,6 +166,27 @@ def shear_diagnostics(f: np.ndarray, p: dict) -> dict:
     out = np.zeros(2)
     bad = lib.lbo_shear_diagnostics(_dp(f), nx, ny, _dp(params_vector(p)), _dp(out))
     return {"U_k": float(out[0]), "I_AB": float(out[1]), "bad": int(bad)}
+
+
+def phi_overlap(f_w: np.ndarray, f: np.ndarray) -> tuple[float, float]:
+    """The two sums of the ageing overlap, Eq. (CORRE), of one realisation:
+    (sum phi(t_w) phi(t_w + dt_w), sum phi(t_w)^2), phi = rho_A - rho_B, for the
+    states f_w (at t_w) and f (dt_w later), both f[2, 9, ny, nx]."""
+    lib = _load()
+    f_w = np.ascontiguousarray(f_w, dtype=np.float64)
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    assert f_w.shape == f.shape
+    _, _, ny, nx = f.shape
+    out = np.zeros(2)
+    lib.lbo_phi_overlap(_dp(f_w), _dp(f), nx, ny, _dp(out))
+    return float(out[0]), float(out[1])
+
+
+def overlap_C(pairs) -> float:
+    """C(t_w, dt_w) of Eq. (CORRE) over an ensemble: the ratio of the two sums,
+    each averaged over the realisations (pairs of (f_w, f))."""
+    sums = np.array([phi_overlap(fw, f) for fw, f in pairs])
+    return float(sums[:, 0].mean() / sums[:, 1].mean())
 
 
 def philox4x32_10(ctr, key):

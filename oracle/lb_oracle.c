@@ -440,6 +440,32 @@ long lbo_shear_diagnostics(const double *f, int nx, int ny, const double *prm, d
   return bad;
 }
 
+/* ---- Ageing overlap (Sec. VII, Eq. (CORRE)).
+ *   phi = rho_A - rho_B, the order parameter of the overlap.
+ *   out[0] = sum_{x,y} phi(x,y; t_w) phi(x,y; t_w + dt_w)
+ *   out[1] = sum_{x,y} phi(x,y; t_w)^2
+ * of one realisation: f_w is the state at the waiting time t_w, f the state
+ * dt_w steps later.  C(t_w, dt_w) of Eq. (CORRE) is the ratio of the two sums,
+ * each averaged over an ensemble of realisations (the caller's average). ---- */
+void lbo_phi_overlap(const double *f_w, const double *f, int nx, int ny, double *out) {
+  const size_t N = (size_t)nx * ny;
+  double num = 0.0, den = 0.0;
+  for (size_t r = 0; r < N; ++r) {
+    double rho_w[2] = {0.0, 0.0}, rho_t[2] = {0.0, 0.0};
+    for (int s = 0; s < 2; ++s)
+      for (int i = 0; i < 9; ++i) {
+        rho_w[s] += f_w[(size_t)(s * 9 + i) * N + r];
+        rho_t[s] += f[(size_t)(s * 9 + i) * N + r];
+      }
+    const double phi_w = rho_w[0] - rho_w[1];
+    const double phi_t = rho_t[0] - rho_t[1];
+    num += phi_w * phi_t;
+    den += phi_w * phi_w;
+  }
+  out[0] = num;
+  out[1] = den;
+}
+
 /* ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers:
  * as easy as 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplies with the
  * round keys bumped by the Weyl constants between rounds. ---- */

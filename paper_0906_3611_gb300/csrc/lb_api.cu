@@ -55,17 +55,8 @@ extern "C" size_t lb_state_bytes(int nx, int ny, int storage) {
 static int validate(int nx, int ny, const lb_params* p) {
   if (!p || nx < 5 || ny < 5) return LB_EINVAL;
   if ((long long)nx * ny > (1LL << 40)) return LB_EINVAL;
-  if (!(p->tau[0] > 0.5) || !(p->tau[1] > 0.5)) return LB_EINVAL;
-  if (!(p->rho0 > 0.0) || !isfinite(p->rho0)) return LB_EINVAL;
-  if (p->boundary != LB_PERIODIC && p->boundary != LB_COUETTE) return LB_EINVAL;
-  if (elem_size(p->storage) == 0) return LB_EINVAL;
   if (p->init_kind != LB_INIT_UNIFORM_NOISE && p->init_kind != LB_INIT_BERNOULLI) return LB_EINVAL;
-  if (p->g_kolmo != 0.0 && p->k_kolmo < 1) return LB_EINVAL;
-  const double vals[] = {p->G_AB, p->Ga[0], p->Ga[1], p->Gr[0], p->Gr[1], p->U_wall,
-                         p->rho_ref[0], p->rho_ref[1], p->tau[0], p->tau[1], p->g_kolmo};
-  for (double v : vals)
-    if (!isfinite(v)) return LB_EINVAL;
-  return LB_OK;
+  return validate_physics(p);
 }
 
 static void fill_phys(lb_handle* h) {

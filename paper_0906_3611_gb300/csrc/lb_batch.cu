@@ -881,30 +881,44 @@ extern "C" int lb_batch_autotune(lb_batch* b, int steps_per_candidate, int* layo
                                  int* rows_per_item) {
   if (!b || steps_per_candidate < 1) return LB_EINVAL;
   NvtxRange range("lb_batch_autotune");
-  // (layout, longest piece): contiguous or packed work lists, uncut or cut
-  const int cands[][2] = {{0, 1 << 30}, {0, 512}, {1, 1 << 30}, {1, 512},
+  // (layout, longest piece): the incumbent first, then contiguous, packed and
+  // wave work lists, uncut or cut.  A candidate replaces the best so far only
+  // when it is at least 2 % faster (short timings are noisy), and a candidate
+  // whose launch fails is skipped.
+  const int cands[][2] = {{b->layout, b->rows_per_item},
+                          {0, 1 << 30}, {0, 512}, {1, 1 << 30}, {1, 512},
                           {1, 128},    {2, 512}, {2, 256},     {2, 128}};
   float best_ms = -1.0f;
   int best_l = b->layout, best_r = b->rows_per_item;
   cudaEvent_t e0, e1;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return LB_ECUDA;
-  for (const auto& c : cands) {
-    b->layout = c[0];
-    b->rows_per_item = c[1];
+  if (cudaEventCreate(&e0) != cudaSuccess) return LB_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return LB_ECUDA;
+  }
+  int rc = LB_OK;
+  for (int c = 0; c < (int)(sizeof(cands) / sizeof(cands[0])); ++c) {
+    if (c > 0 && cands[c][0] == cands[0][0] && cands[c][1] == cands[0][1]) continue;
+    b->layout = cands[c][0];
+    b->rows_per_item = cands[c][1];
     b->dirty = true;
-    int rc = rebuild_items(b);
+    rc = rebuild_items(b);
     if (rc) break;
-    if (batch_launch(b, b->stream) != cudaSuccess) break;  // warm-up with this list
-    cudaEventRecord(e0, b->stream);
-    for (int k = 0; k < steps_per_candidate; ++k) batch_launch(b, b->stream);
-    cudaEventRecord(e1, b->stream);
-    if (cudaEventSynchronize(e1) != cudaSuccess) break;
+    bool ok = batch_launch(b, b->stream) == cudaSuccess;  // warm-up with this list
+    if (ok) ok = cudaEventRecord(e0, b->stream) == cudaSuccess;
+    for (int k = 0; ok && k < steps_per_candidate; ++k) ok = batch_launch(b, b->stream) == cudaSuccess;
+    if (ok) ok = cudaEventRecord(e1, b->stream) == cudaSuccess;
+    if (ok) ok = cudaEventSynchronize(e1) == cudaSuccess;
     float ms = 0.0f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (best_ms < 0.0f || ms < best_ms) {
+    if (ok) ok = cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      continue;
+    }
+    if (best_ms < 0.0f || ms < 0.98f * best_ms) {
       best_ms = ms;
-      best_l = c[0];
-      best_r = c[1];
+      best_l = cands[c][0];
+      best_r = cands[c][1];
     }
   }
   cudaEventDestroy(e0);
@@ -912,8 +926,9 @@ extern "C" int lb_batch_autotune(lb_batch* b, int steps_per_candidate, int* layo
   b->layout = best_l;
   b->rows_per_item = best_r;
   b->dirty = true;
-  int rc = rebuild_items(b);
+  const int rc2 = rebuild_items(b);
   if (rc) return rc;
+  if (rc2) return rc2;
   if (layout) *layout = best_l;
   if (rows_per_item) *rows_per_item = best_r;
   return best_ms < 0.0f ? LB_ECUDA : LB_OK;

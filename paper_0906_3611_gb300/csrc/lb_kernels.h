@@ -28,6 +28,26 @@ struct PhysD {
   int dev;  // 1 for the deviation storages (every storage but FP64)
 };
 
+// Checks of the physics part of lb_params shared by every entry point that
+// takes one: tau_s > 1/2, rho0 > 0, a known boundary and storage, a Kolmogorov
+// wave number >= 1 when the body force is on, and finite couplings, wall
+// speed, reference densities and force amplitude.  LB_OK or LB_EINVAL.
+inline int validate_physics(const lb_params* p) {
+  if (!p) return LB_EINVAL;
+  if (!(p->tau[0] > 0.5) || !(p->tau[1] > 0.5)) return LB_EINVAL;
+  if (!(p->rho0 > 0.0) || !isfinite(p->rho0)) return LB_EINVAL;
+  if (p->boundary != LB_PERIODIC && p->boundary != LB_COUETTE) return LB_EINVAL;
+  if (p->storage != LB_F64 && p->storage != LB_F32 && p->storage != LB_BF16_DEV &&
+      p->storage != LB_F16_DEV)
+    return LB_EINVAL;
+  if (p->g_kolmo != 0.0 && p->k_kolmo < 1) return LB_EINVAL;
+  const double vals[] = {p->G_AB, p->Ga[0], p->Ga[1], p->Gr[0], p->Gr[1], p->U_wall,
+                         p->rho_ref[0], p->rho_ref[1], p->tau[0], p->tau[1], p->g_kolmo};
+  for (double v : vals)
+    if (!isfinite(v)) return LB_EINVAL;
+  return LB_OK;
+}
+
 // Every storage but FP64 holds deviations d_i = f_i - w_i rho_ref,s: rounding
 // errors then scale with |d_i| instead of |f_i| (FP32 with rho_ref = 0 stores
 // plain populations).  FP64 stores plain populations.
@@ -109,6 +129,10 @@ cudaError_t launch_observe(int storage, const void* src, const Geom& g, const Ph
                            Status* status, double* partials, int cap_blocks, double* out,
                            cudaStream_t st);
 int observe_blocks(const Geom& g);
+// The first half of launch_observe: per-block partial sums only (no finalize).
+cudaError_t launch_observe_partials(int storage, const void* src, const Geom& g, const PhysD& ph,
+                                    Status* status, double* partials, int cap_blocks,
+                                    cudaStream_t st);
 
 // Shear diagnostics of FP64 fields (as launch_fields writes them) at wave
 // number k: out[0] = U_k, out[1] = I_AB (Sec. VII).  `partials` holds

@@ -10,6 +10,10 @@
 // sums in one fixed, file-scope device array instead.  The paper has no
 // counterpart: it is a library-interface concern only.
 //
+// The arithmetic is the handle path's own observe kernel (lb_tile.cu), given
+// the static array as its partial-sum area and status word; only the final
+// normalisation into out[] is done here.
+//
 // The array is static device memory of this library: every GPU that loads
 // liblb.so holds it (4 MiB + 64 B) until the process exits.  All calls share
 // it, so calls whose work overlaps on the GPU (two streams, or two host
@@ -18,154 +22,25 @@
 
 #include "lb.h"
 #include "lb_kernels.h"
-#include "lb_site.cuh"
 
 namespace lbk {
 namespace {
 
-constexpr int NA_TX = 32, NA_TY = 8;
-constexpr int NA_EX = NA_TX + 4, NA_EY = NA_TY + 4;
-constexpr int NA_THREADS = NA_TX * NA_TY;
-// One partial-sum record of NOBS doubles per 32 x 8 tile; 65536 tiles cover
-// e.g. a 4096 x 4096 lattice.  Larger lattices are rejected (LB_ETOOBIG).
+// One partial-sum record of NOBS doubles per 32 x 8 tile of the observe
+// kernel; 65536 tiles cover e.g. a 4096 x 4096 lattice.  Larger lattices are
+// rejected (LB_ETOOBIG).
 constexpr int kMaxTiles = 65536;
-constexpr int kStatusSlot = kMaxTiles * NOBS;  // one double-sized slot: bad-density counter
+constexpr int kStatusSlot = kMaxTiles * NOBS;  // 8 doubles: the kernel's status word
+static_assert(sizeof(Status) <= 8 * sizeof(double), "status word fits the tail");
 
 }  // namespace
 }  // namespace lbk
 
-// The scratch: per-tile partial sums, then the status counter.
+// The scratch: per-tile partial sums, then the status word.
 static __device__ __align__(256) double g_noalloc_scratch[lbk::kMaxTiles * lbk::NOBS + 8];
 
 namespace lbk {
 namespace {
-
-template <int STORAGE>
-__global__ void __launch_bounds__(NA_THREADS)
-    k_observe_static(const typename Store<STORAGE>::T* __restrict__ src, Geom g,
-                     Phys<typename Store<STORAGE>::C> ph, double* __restrict__ scratch) {
-  using S = Store<STORAGE>;
-  using T = typename S::T;
-  using C = typename S::C;
-  __shared__ C s_rho[2][NA_EY][NA_EX];
-  __shared__ C s_psi[2][NA_EY][NA_EX];
-  __shared__ double red[NOBS][NA_THREADS];
-
-  const int x0 = blockIdx.x * NA_TX, y0 = blockIdx.y * NA_TY;
-  const int tid = threadIdx.x;
-  for (int e = tid; e < NA_EX * NA_EY; e += NA_THREADS) {
-    const int ex = e % NA_EX, ey = e / NA_EX;
-    const int gx = wrapi(x0 + ex - 2, g.nx);
-    const int gy = stencil_row(y0 + ey - 2, g.ny, g.boundary);
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      C dr = C(0);
-#pragma unroll
-      for (int i = 0; i < 9; ++i) dr += S::ld(src[lidx(g, s, i, gy, gx)]);
-      s_rho[s][ey][ex] = ph.rho_ref[s] + dr;
-      s_psi[s][ey][ex] = ph.rho0 * (C(1) - ph.E[s] * exp_c<C>(-dr * ph.inv_rho0));
-    }
-  }
-  __syncthreads();
-
-  const int tx = tid % NA_TX, ty = tid / NA_TX;
-  const int x = x0 + tx, y = y0 + ty;
-  double acc[NOBS];
-#pragma unroll
-  for (int k = 0; k < NOBS; ++k) acc[k] = 0.0;
-  int bad = 0;
-  if (x < g.nx && y < g.ny) {
-    C d[2][9];
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-      for (int i = 0; i < 9; ++i) d[s][i] = S::ld(src[lidx(g, s, i, y, x)]);
-    C drho[2], rho[2];
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      C a = C(0);
-#pragma unroll
-      for (int i = 0; i < 9; ++i) a += d[s][i];
-      drho[s] = a;
-      rho[s] = ph.rho_ref[s] + a;
-    }
-    const C gb = body_accel(ph, y, g.ny);  // Kolmogorov body acceleration of the row
-    C Fx[2], Fy[2];
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      C sx = C(0), sy = C(0), xx = C(0), xy = C(0);
-#pragma unroll
-      for (int dy = -2; dy <= 2; ++dy)
-#pragma unroll
-        for (int dx = -2; dx <= 2; ++dx) {
-          if (dx == 0 && dy == 0) continue;
-          const int k = group_of(dx, dy);
-          const C ps = s_psi[s][ty + 2 + dy][tx + 2 + dx];
-          sx += ph.Wpsi[s][k] * ps * C(dx);
-          sy += ph.Wpsi[s][k] * ps * C(dy);
-          if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) {
-            const C ro = s_rho[1 - s][ty + 2 + dy][tx + 2 + dx];
-            xx += ph.gw[k] * ro * C(dx);
-            xy += ph.gw[k] * ro * C(dy);
-          }
-        }
-      const C pc = s_psi[s][ty + 2][tx + 2];
-      Fx[s] = -pc * sx - rho[s] * xx + rho[s] * gb;
-      Fy[s] = -pc * sy - rho[s] * xy;
-    }
-    C jx[2], jy[2];
-    momenta<C>(d, jx, jy);
-    C vx[2], vy[2];
-    shifted_velocities<C>(ph, rho, jx, jy, Fx, Fy, vx, vy, bad);
-    acc[0] = (double)ph.rho_ref[0] + (double)drho[0];
-    acc[1] = (double)ph.rho_ref[1] + (double)drho[1];
-    acc[2] = (double)jx[0] + (double)jx[1];
-    acc[3] = (double)jy[0] + (double)jy[1];
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      const C usq15 = C(1.5) * (vx[s] * vx[s] + vy[s] * vy[s]);
-      double neq_xy = 0.0;
-#pragma unroll
-      for (int i = 5; i < 9; ++i) {
-        const C deq = eq_dev<C>(i, drho[s], rho[s], vx[s], vy[s], usq15);
-        neq_xy += (double)(d[s][i] - deq) * (double)(Q9::cx(i) * Q9::cy(i));
-      }
-      acc[4] -= (1.0 - 0.5 * (double)ph.omega[s]) * neq_xy;
-      if (g.boundary == LB_COUETTE && (y == 0 || y == g.ny - 1)) {
-#pragma unroll
-        for (int i = 1; i < 9; ++i) {
-          const int yd = y + Q9::cy(i);
-          if (yd >= 0 && yd < g.ny) continue;
-          const C deq = eq_dev<C>(i, drho[s], rho[s], vx[s], vy[s], usq15);
-          const C dstar = d[s][i] + ph.omega[s] * (deq - d[s][i]);
-          const double fp = (double)(wq<C>(i) * ph.rho_ref[s] + dstar);
-          const C Uw = (yd >= g.ny) ? ph.Uwall : -ph.Uwall;
-          const double back = fp - (double)wall_term<C>(i, rho[s], Uw);
-          const double push = (double)Q9::cx(i) * (fp + back);
-          if (yd >= g.ny)
-            acc[5] -= push;
-          else
-            acc[6] += push;
-        }
-      }
-    }
-  }
-  if (bad) atomicAdd((unsigned int*)(scratch + kStatusSlot), (unsigned)bad);
-#pragma unroll
-  for (int k = 0; k < NOBS; ++k) red[k][tid] = acc[k];
-  __syncthreads();
-  for (int stride = NA_THREADS / 2; stride > 0; stride >>= 1) {
-    if (tid < stride) {
-#pragma unroll
-      for (int k = 0; k < NOBS; ++k) red[k][tid] += red[k][tid + stride];
-    }
-    __syncthreads();
-  }
-  if (tid < NOBS) {
-    const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
-    scratch[b * NOBS + tid] = red[tid][0];
-  }
-}
 
 // Sum the per-tile records in a fixed order and write the normalised results.
 __global__ void __launch_bounds__(256)
@@ -197,36 +72,85 @@ __global__ void __launch_bounds__(256)
     out[4] = red[4][0] / ((double)nx * (double)ny);
     out[5] = couette ? red[5][0] / nx : 0.0;
     out[6] = couette ? red[6][0] / nx : 0.0;
-    out[7] = (double)*(const unsigned int*)(scratch + kStatusSlot);
+    out[7] = (double)reinterpret_cast<const Status*>(scratch + kStatusSlot)->bad_rho;
   }
 }
 
-template <int STORAGE>
-cudaError_t observe_static_t(const void* f, const Geom& g, const PhysD& pd, double* scratch,
-                             dim3 grid, cudaStream_t st) {
-  using S = Store<STORAGE>;
-  k_observe_static<STORAGE><<<grid, NA_THREADS, 0, st>>>((const typename S::T*)f, g,
-                                                         make_phys<typename S::C>(pd), scratch);
-  return cudaGetLastError();
-}
+// ---- the scratch array's device address ----
+// cudaGetSymbolAddress answers for the calling thread's current context.  A
+// call outside stream capture always asks afresh (so a device reset or a
+// different context on the same device never sees a stale address) and
+// remembers the answer under the context's process-unique id; a call made
+// while its stream is capturing uses the remembered address of its context.
+using CtxGetCurrentFn = int (*)(void**);                     // cuCtxGetCurrent
+using CtxGetIdFn = int (*)(void*, unsigned long long*);      // cuCtxGetId
 
-// Device address of the scratch array, looked up once per device.
 std::mutex g_mu;
-double* g_addr[256] = {};
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+bool g_entry_points_looked_up = false;
+constexpr int kCacheSlots = 16;
+unsigned long long g_ctx_ids[kCacheSlots] = {};
+double* g_ctx_addr[kCacheSlots] = {};
+int g_next_slot = 0;
 
-int scratch_address(double** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return LB_ECUDA;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
-    void* ptr = nullptr;
-    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
-      cudaGetLastError();
-      return LB_ECUDA;
-    }
-    g_addr[dev] = (double*)ptr;
+// Process-unique id of the current context, 0 if the driver does not say.
+// (called with g_mu held)
+unsigned long long current_context_id() {
+  if (!g_entry_points_looked_up) {
+    g_entry_points_looked_up = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_ctx_current = (CtxGetCurrentFn)f;
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_ctx_id = (CtxGetIdFn)f;
+    cudaGetLastError();
   }
-  *out = g_addr[dev];
+  if (!g_ctx_current || !g_ctx_id) return 0;
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (g_ctx_current(&ctx) != 0 || !ctx || g_ctx_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+int scratch_address(cudaStream_t st, double** out) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return LB_ECUDA;
+  }
+  std::lock_guard<std::mutex> lock(g_mu);
+  const unsigned long long id = current_context_id();
+  if (cs != cudaStreamCaptureStatusNone && id != 0) {
+    for (int k = 0; k < kCacheSlots; ++k)
+      if (g_ctx_ids[k] == id) {
+        *out = g_ctx_addr[k];
+        return LB_OK;
+      }
+  }
+  void* ptr = nullptr;
+  if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+    cudaGetLastError();
+    return LB_ECUDA;
+  }
+  *out = (double*)ptr;
+  if (id != 0) {
+    int slot = -1;
+    for (int k = 0; k < kCacheSlots; ++k)
+      if (g_ctx_ids[k] == id) slot = k;
+    if (slot < 0) {
+      slot = g_next_slot;
+      g_next_slot = (g_next_slot + 1) % kCacheSlots;
+    }
+    g_ctx_ids[slot] = id;
+    g_ctx_addr[slot] = (double*)ptr;
+  }
   return LB_OK;
 }
 
@@ -236,17 +160,8 @@ int scratch_address(double** out) {
 extern "C" int lb_observables_noalloc(const void* f, int nx, int ny, int pitch, const lb_params* p,
                                       void* cuda_stream, double* out) {
   using namespace lbk;
-  if (!f || !p || !out || nx < 5 || ny < 5 || pitch < nx) return LB_EINVAL;
-  if (!(p->tau[0] > 0.5) || !(p->tau[1] > 0.5) || !(p->rho0 > 0.0)) return LB_EINVAL;
-  if (p->boundary != LB_PERIODIC && p->boundary != LB_COUETTE) return LB_EINVAL;
-  if (elem_size(p->storage) == 0) return LB_EINVAL;
-  const long long tx = (nx + NA_TX - 1) / NA_TX, ty = (ny + NA_TY - 1) / NA_TY;
-  if (tx * ty > kMaxTiles) return LB_ETOOBIG;
-
-  double* scratch = nullptr;
-  int rc = scratch_address(&scratch);
-  if (rc) return rc;
-  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (!f || !out || nx < 5 || ny < 5 || pitch < nx) return LB_EINVAL;
+  if (validate_physics(p) != LB_OK) return LB_EINVAL;
 
   Geom g;
   g.nx = nx;
@@ -254,20 +169,25 @@ extern "C" int lb_observables_noalloc(const void* f, int nx, int ny, int pitch, 
   g.pitch = pitch;
   g.boundary = p->boundary;
   g.plane = (long long)ny * pitch;
+  // the observe kernel's tiles are 32 x 8 sites
+  const long long tiles = (long long)((nx + 31) / 32) * (long long)((ny + 7) / 8);
+  if (tiles > kMaxTiles) return LB_ETOOBIG;
+  const int ntiles = observe_blocks(g);
+  if (ntiles != (int)tiles) return LB_ECUDA;  // (the tiling above is the kernel's)
+
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  double* scratch = nullptr;
+  int rc = scratch_address(st, &scratch);
+  if (rc) return rc;
   const PhysD d = physd_from_params(*p);
 
-  // the status counter must start at zero; every partial record is overwritten
-  if (cudaMemsetAsync(scratch + kStatusSlot, 0, sizeof(double), st) != cudaSuccess) return LB_ECUDA;
-  const dim3 grid((unsigned)tx, (unsigned)ty);
-  cudaError_t e = cudaErrorInvalidValue;
-  switch (p->storage) {
-    case LB_F64: e = observe_static_t<LB_F64>(f, g, d, scratch, grid, st); break;
-    case LB_F32: e = observe_static_t<LB_F32>(f, g, d, scratch, grid, st); break;
-    case LB_BF16_DEV: e = observe_static_t<LB_BF16_DEV>(f, g, d, scratch, grid, st); break;
-    case LB_F16_DEV: e = observe_static_t<LB_F16_DEV>(f, g, d, scratch, grid, st); break;
-  }
-  if (e != cudaSuccess) return LB_ECUDA;
-  k_finalize_static<<<1, 256, 0, st>>>(scratch, (int)(tx * ty), nx, ny,
+  // the status word must start at zero; every partial record is overwritten
+  if (cudaMemsetAsync(scratch + kStatusSlot, 0, 8 * sizeof(double), st) != cudaSuccess)
+    return LB_ECUDA;
+  if (launch_observe_partials(p->storage, f, g, d, reinterpret_cast<Status*>(scratch + kStatusSlot),
+                              scratch, kMaxTiles, st) != cudaSuccess)
+    return LB_ECUDA;
+  k_finalize_static<<<1, 256, 0, st>>>(scratch, ntiles, nx, ny,
                                        p->boundary == LB_COUETTE ? 1 : 0, out);
   return cudaGetLastError() == cudaSuccess ? LB_OK : LB_ECUDA;
 }

@@ -473,20 +473,25 @@ static cudaError_t observe_t(const void* src, const Geom& g, const PhysD& pd, St
   return cudaGetLastError();
 }
 
+cudaError_t launch_observe_partials(int storage, const void* src, const Geom& g, const PhysD& ph,
+                                    Status* status, double* partials, int cap_blocks,
+                                    cudaStream_t st) {
+  if (observe_blocks(g) > cap_blocks) return cudaErrorInvalidValue;
+  switch (storage) {
+    case LB_F64: return observe_t<LB_F64>(src, g, ph, status, partials, st);
+    case LB_F32: return observe_t<LB_F32>(src, g, ph, status, partials, st);
+    case LB_BF16_DEV: return observe_t<LB_BF16_DEV>(src, g, ph, status, partials, st);
+    case LB_F16_DEV: return observe_t<LB_F16_DEV>(src, g, ph, status, partials, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_observe(int storage, const void* src, const Geom& g, const PhysD& ph,
                            Status* status, double* partials, int cap_blocks, double* out,
                            cudaStream_t st) {
-  const int nb = observe_blocks(g);
-  if (nb > cap_blocks) return cudaErrorInvalidValue;
-  cudaError_t e = cudaErrorInvalidValue;
-  switch (storage) {
-    case LB_F64: e = observe_t<LB_F64>(src, g, ph, status, partials, st); break;
-    case LB_F32: e = observe_t<LB_F32>(src, g, ph, status, partials, st); break;
-    case LB_BF16_DEV: e = observe_t<LB_BF16_DEV>(src, g, ph, status, partials, st); break;
-    case LB_F16_DEV: e = observe_t<LB_F16_DEV>(src, g, ph, status, partials, st); break;
-  }
+  const cudaError_t e = launch_observe_partials(storage, src, g, ph, status, partials, cap_blocks, st);
   if (e != cudaSuccess) return e;
-  k_finalize<<<1, 256, 0, st>>>(partials, nb, out);
+  k_finalize<<<1, 256, 0, st>>>(partials, observe_blocks(g), out);
   return cudaGetLastError();
 }
 

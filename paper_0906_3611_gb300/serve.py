@@ -185,7 +185,7 @@ class Server:
             return []
         running = frozenset((slot, req.rid) for slot, (req, _) in self.active.items())
         if self.retune and running != self._tuned_for:
-            self.batch.autotune(1)
+            self.batch.autotune(2)
             self._tuned_for = running
         self.batch.run(self.chunk)
         remaining, done = self.batch.poll()

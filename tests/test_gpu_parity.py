@@ -5,7 +5,10 @@
   boundary kinds, unequal tau and species couplings; 1000 steps of the 64 x 64
   parity configuration are checked step by step from identical states.
 * The seeded initial state is bit-identical to the oracle's.
-* FP32 storage: max relative density error <= 1e-5 after 100 steps.
+* FP32 storage: max relative density error <= 1e-5 after 100 steps on stable
+  states; on the unstable (spinodal) parity configuration every step is
+  within 1e-5 of the oracle's and the free run within the envelope of the
+  oracle's own propagation of those one-step errors.
 * Observables (mass, momentum, sigma_xy, wall stresses, fields) agree to 1e-12.
 * At the benchmark size (4096 x 4096 Couette, FP32) sampled sites of one step
   are checked against the oracle run on a local patch (the new populations of
@@ -154,22 +157,73 @@ def test_fp32_density_error_on_a_stable_state_after_100_steps(lb):
     assert _rel_err(rho_gpu, ref) <= 1e-5
 
 
-def test_fp32_density_error_config_run(lb):
-    """64 x 64 parity configuration (rho = 1 +- 0.05, spinodal).  The uniform
-    state is unstable: in FP64 a single 1e-7 perturbation of the initial state
-    grows to ~2e-4 of the density in 100 steps, so FP32 is held to 1e-5 for the
-    first 20 steps and, at 100 steps, to within 30x of that FP64 spread (FP32
-    rounds every population at every step, not once at the start; a wrong force
-    or collision term gives errors of order one)."""
+def _rho_err(f, ref):
+    """Max relative density error of state f against state ref."""
+    return _rel_err(f.sum(axis=1), ref.sum(axis=1))
+
+
+def test_fp32_config_run_is_its_one_step_errors_propagated(lb):
+    """64 x 64 parity configuration (rho = 1 +- 0.05): the uniform state is
+    linearly unstable (spinodal), so any perturbation grows -- in FP64 a single
+    1e-7 perturbation of the start reaches ~2e-4 of the density after 100
+    steps -- and no FP32 implementation can hold the free run to 1e-5.  The
+    bound is derived instead of fixed:
+
+    1. every step of the run, taken by the GPU from the oracle's state (rounded
+       to FP32), is within the FP32 bar of the oracle's step: the one-step
+       error e_t, measured against each population's rest-state scale
+       w_i rho_s, is <= 1e-5;
+    2. the oracle propagates those one-step errors: the shadow run
+       h_{t+1} = oracle_step(h_t) + e_t injects the GPU's own error fields,
+       and seven more runs inject them with random signs per element;
+    3. the GPU's free run stays within that ensemble's envelope, max + 4 sd
+       over the eight runs, at t = 20, 40, ..., 100 -- a wrong force or
+       collision term breaks step 1, and an error growing faster than the
+       oracle's own dynamics breaks step 3 at the later times.
+    The first 20 steps are also held to 1e-5 directly."""
     nx = ny = 64
+    T, marks = 100, (20, 40, 60, 80, 100)
     f0 = oracle.init_state(nx, ny, 0, 0, (1.0, 1.0, 0.05)).astype(np.float32).astype(np.float64)
-    ref20 = oracle.observables(oracle.step(f0, CFG, 20)[0], CFG)["rho"]
-    assert _rel_err(_fp32_rho_after(lb, f0, CFG, 20), ref20) <= 1e-5
-    ref100 = oracle.observables(oracle.step(f0, CFG, 100)[0], CFG)["rho"]
-    pert = f0 * (1.0 + 1e-7 * inputs.rng(5).uniform(-1.0, 1.0, f0.shape))
-    spread = _rel_err(oracle.observables(oracle.step(pert, CFG, 100)[0], CFG)["rho"], ref100)
-    err = _rel_err(_fp32_rho_after(lb, f0, CFG, 100), ref100)
-    assert err <= 30.0 * spread
+    traj = [f0]
+    for t in range(T):
+        traj.append(oracle.step(traj[-1], CFG, 1)[0])
+    lat = lb.Lattice(nx, ny, _params(lb, CFG, lb.LB_F32))
+    errs = []
+    worst = 0.0
+    for t in range(T):
+        ft = traj[t].astype(np.float32).astype(np.float64)
+        g = lat.set_state(ft).step(1).get_state()
+        ref = oracle.step(ft, CFG, 1)[0]
+        worst = max(worst, _scaled_err(g, ref))
+        errs.append(g - ref)
+    assert lat.status() == lb.LB_OK
+    assert worst <= 1e-5  # step 1: the FP32 bar, every step
+    # the GPU's free run from the same start
+    free = {}
+    lat.set_state(f0)
+    for t in marks:
+        lat.step(t - lat.time)
+        free[t] = _rho_err(lat.get_state(), traj[t])
+    assert lat.status() == lb.LB_OK
+    lat.close()
+    assert free[20] <= 1e-5
+    # step 2: the oracle's propagation of the one-step errors
+    rng = inputs.rng(17)
+    members = []
+    for k in range(8):
+        h = f0.copy()
+        d = {}
+        for t in range(T):
+            e = errs[t] if k == 0 else errs[t] * rng.choice((-1.0, 1.0), size=errs[t].shape)
+            h = oracle.step(h, CFG, 1)[0] + e
+            if t + 1 in marks:
+                d[t + 1] = _rho_err(h, traj[t + 1])
+        members.append(d)
+    for t in marks:  # step 3
+        D = np.array([m[t] for m in members])
+        bound = D.max() + 4.0 * D.std()
+        assert free[t] <= bound, (t, free[t], D)
+    assert free[100] > 1e-5  # (the instability is real: the 1e-5 bar cannot apply here)
 
 
 def test_fp32_couette_shear_flow_after_100_steps(lb):

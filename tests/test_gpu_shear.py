@@ -6,6 +6,7 @@
   U_k + g/2 = g / (nu k^2) to fourth order at tau = 1.
 * lb_shear_diagnostics equals the oracle's diagnostics of the same state
   (U_k and I_AB to 1e-12 for FP64 storage).
+* lb_phi_overlap equals the oracle's overlap sums (Eq. (CORRE)) to 1e-12.
 * A batched replica with the body force equals the lattice run alone.
 """
 import numpy as np
@@ -118,26 +119,33 @@ def test_batched_kolmogorov_replicas_equal_the_lattice_alone(lb, monkeypatch):
         lat.close()
 
 
-def test_ageing_overlap_matches_its_definition(lb):
-    """Eq. (CORRE) terms: sum phi(t_w) phi(t) and sum phi(t_w)^2, phi = rho_A - rho_B."""
+def test_ageing_overlap_matches_the_oracle(lb):
+    """Eq. (CORRE) sums of lb_phi_overlap against the oracle's on two states of
+    an FP64 Kolmogorov-sheared trajectory that the oracle ran (t_w = 200 and
+    t_w + 150 from the seeded start), to 1e-12 relative; the snapshot survives
+    the state exchange, and C(t_w, 0) = 1."""
     nx, ny = 136, 48
+    op = dict(STD07, g_kolmo=1e-4, k_kolmo=1)
+    f0 = oracle.init_state(nx, ny, 8, oracle.INIT_UNIFORM_NOISE, (0.612, 0.612, 0.01))
+    f_w, _ = oracle.step(f0, op, 200)
+    f_t, _ = oracle.step(f_w, op, 150)
+    num_ref, den_ref = oracle.phi_overlap(f_w, f_t)
     p = lb.make_params(**STD07, storage=lb.LB_F64, rho_ref=(0.6, 0.6),
                        init_kind=lb.LB_INIT_UNIFORM_NOISE, init=(0.612, 0.612, 0.01),
                        g_kolmo=1e-4, k_kolmo=1)
     lat = lb.Lattice(nx, ny, p).init_random(8)
+    assert np.array_equal(lat.get_state(), f0)
     with pytest.raises(lb.LBError):
         lat.phi_overlap()  # no snapshot yet
-    lat.step(200).phi_snapshot()
+    lat.set_state(f_w).phi_snapshot()
     num0, den0 = lat.phi_overlap()
-    assert num0 == den0 > 0  # C(t_w, 0) = 1
-    rho_w = lat.observables(fields=True)["rho"]
-    lat.step(150)
+    assert num0 == den0  # C(t_w, 0) = 1
+    assert den0 == pytest.approx(den_ref, rel=1e-12)
+    lat.set_state(f_t)
     num, den = lat.phi_overlap()
-    rho_t = lat.observables(fields=True)["rho"]
     lat.close()
-    phi_w, phi_t = rho_w[0] - rho_w[1], rho_t[0] - rho_t[1]
-    assert den == pytest.approx(float(np.sum(phi_w * phi_w)), rel=1e-12)
-    assert num == pytest.approx(float(np.sum(phi_w * phi_t)), rel=1e-12)
+    assert den == pytest.approx(den_ref, rel=1e-12)
+    assert num == pytest.approx(num_ref, rel=1e-12)
     assert 0.0 < num / den < 1.0  # the configuration has moved
 
 
