@@ -157,6 +157,17 @@ def test_fp32_density_error_on_a_stable_state_after_100_steps(lb):
     assert _rel_err(rho_gpu, ref) <= 1e-5
 
 
+def _storage_scaled_err(g, ref, rho_ref):
+    """Error of each population relative to the scale its FP32 deviation is
+    stored at, w_i max(rho_s(r), rho_ref,s): the storage holds
+    d_i = f_i - w_i rho_ref,s, so a dilute site (rho_s << rho_ref) keeps FP32
+    precision relative to w_i rho_ref, not to its own w_i rho_s."""
+    rho = np.abs(ref.sum(axis=1))
+    rr = np.asarray(rho_ref, dtype=np.float64)[:, None, None]
+    scale = W9[None, :, None, None] * np.maximum(rho, rr)[:, None]
+    return float(np.max(np.abs(g - ref) / scale))
+
+
 def _rho_err(f, ref):
     """Max relative density error of state f against state ref."""
     return _rel_err(f.sum(axis=1), ref.sum(axis=1))
@@ -171,8 +182,9 @@ def test_fp32_config_run_is_its_one_step_errors_propagated(lb):
 
     1. every step of the run, taken by the GPU from the oracle's state (rounded
        to FP32), is within the FP32 bar of the oracle's step: the one-step
-       error e_t, measured against each population's rest-state scale
-       w_i rho_s, is <= 1e-5;
+       error e_t, measured against the scale each population's deviation is
+       stored at, w_i max(rho_s(r), rho_ref,s), is <= 1e-5 (the run separates
+       into phases of density 0.03 to 3 around rho_ref = 1);
     2. the oracle propagates those one-step errors: the shadow run
        h_{t+1} = oracle_step(h_t) + e_t injects the GPU's own error fields,
        and seven more runs inject them with random signs per element;
@@ -194,7 +206,7 @@ def test_fp32_config_run_is_its_one_step_errors_propagated(lb):
         ft = traj[t].astype(np.float32).astype(np.float64)
         g = lat.set_state(ft).step(1).get_state()
         ref = oracle.step(ft, CFG, 1)[0]
-        worst = max(worst, _scaled_err(g, ref))
+        worst = max(worst, _storage_scaled_err(g, ref, (1.0, 1.0)))
         errs.append(g - ref)
     assert lat.status() == lb.LB_OK
     assert worst <= 1e-5  # step 1: the FP32 bar, every step
