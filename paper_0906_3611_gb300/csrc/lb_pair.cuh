@@ -56,6 +56,28 @@ __device__ __forceinline__ P pswap(P a) {
   return r;
 }
 
+// ---- FP32 accumulation of a 16-bit site pair ----
+// The mixed-precision add of sm_100 and later (PTX add.f32.f16 / add.f32.bf16)
+// widens its 16-bit operand exactly and adds it in FP32 with one rounding: the
+// same result as a conversion followed by an FP32 add, in one instruction per
+// species instead of a conversion per species plus a packed add.
+__device__ __forceinline__ float2 pacc(float2 acc, __half2 v) {
+  const uint32_t u = *reinterpret_cast<const uint32_t*>(&v);
+  asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
+      "add.rn.f32.f16 %0, lo, %0;\n\tadd.rn.f32.f16 %1, hi, %1;\n\t}"
+      : "+f"(acc.x), "+f"(acc.y)
+      : "r"(u));
+  return acc;
+}
+__device__ __forceinline__ float2 pacc(float2 acc, __nv_bfloat162 v) {
+  const uint32_t u = *reinterpret_cast<const uint32_t*>(&v);
+  asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
+      "add.rn.f32.bf16 %0, lo, %0;\n\tadd.rn.f32.bf16 %1, hi, %1;\n\t}"
+      : "+f"(acc.x), "+f"(acc.y)
+      : "r"(u));
+  return acc;
+}
+
 // ---- stochastic rounding to 16 bits (used for the rest population only) ----
 // The magnitude is rounded up with probability equal to its distance from the
 // value below, using 16 (BF16) or 13 (FP16) random bits added under the kept
@@ -99,8 +121,9 @@ struct PairStore<LB_BF16_DEV> {
   using T2 = __nv_bfloat162;
   static __device__ __forceinline__ float2 ld(T2 v) { return __bfloat1622float2(v); }
   static __device__ __forceinline__ T2 st(float2 v) { return __float22bfloat162_rn(v); }
+  // species A rounds with the low 16 random bits, B with the high 16
   static __device__ __forceinline__ T2 st_sr(float2 v, uint32_t r) {
-    return __halves2bfloat162(bf16_sr(v.x, r), bf16_sr(v.y, mix32(r)));
+    return __halves2bfloat162(bf16_sr(v.x, r), bf16_sr(v.y, __funnelshift_l(r, r, 16)));
   }
 };
 template <>
@@ -109,7 +132,7 @@ struct PairStore<LB_F16_DEV> {
   static __device__ __forceinline__ float2 ld(T2 v) { return __half22float2(v); }
   static __device__ __forceinline__ T2 st(float2 v) { return __float22half2_rn(v); }
   static __device__ __forceinline__ T2 st_sr(float2 v, uint32_t r) {
-    return __halves2half2(f16_sr(v.x, r), f16_sr(v.y, mix32(r)));
+    return __halves2half2(f16_sr(v.x, r), f16_sr(v.y, __funnelshift_l(r, r, 16)));
   }
 };
 

@@ -384,14 +384,31 @@ struct RowsLoop {
 
   // rho, drho and psi pairs of staged column c (0 .. SW-1) of a staged row
   __device__ __forceinline__ void column(const T2* srow, int c, P& rho, P& psi, P& drho) const {
-    const T2* p = srow + c;
-    P v[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) v[i] = PS::ld(p[i * SW]);
-    const P a = sum9(v);
+    const P a = staged_sum9(srow + c);
     drho = a;
     rho = padd(rho_ref(), a);
     psi = psi_of(a);
+  }
+  // sum of the nine staged populations of a site: a pairwise tree for the
+  // 32/64-bit storages; two chains of mixed-precision adds for the 16-bit ones
+  // (no separate conversion of each value)
+  static __device__ __forceinline__ P staged_sum9(const T2* p) {
+    if constexpr (sizeof(T2) == 4) {
+      P a = PS::ld(p[0]), b = PS::ld(p[5 * SW]);
+      a = pacc(a, p[1 * SW]);
+      b = pacc(b, p[6 * SW]);
+      a = pacc(a, p[2 * SW]);
+      b = pacc(b, p[7 * SW]);
+      a = pacc(a, p[3 * SW]);
+      b = pacc(b, p[8 * SW]);
+      a = pacc(a, p[4 * SW]);
+      return padd(a, b);
+    } else {
+      P v[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) v[i] = PS::ld(p[i * SW]);
+      return sum9(v);
+    }
   }
   // pairwise sum of a site's nine populations (a shorter dependency chain than
   // a running sum; the collision repeats it bit for bit)
@@ -451,12 +468,25 @@ struct RowsLoop {
     psi0 = lag_psi[k0];
   }
 
-  // sum of the eight moving populations as they will be stored (pairwise)
+  // sum of the eight moving populations as they will be stored (pairwise; the
+  // 16-bit storages add the stored values in two mixed-precision chains)
   __device__ __forceinline__ P stored_sum8(const P (&d)[9]) const {
-    P v[9];
+    if constexpr (sizeof(T2) == 4) {
+      P a = PS::ld(PS::st(d[1])), b = PS::ld(PS::st(d[5]));
+      a = pacc(a, PS::st(d[2]));
+      b = pacc(b, PS::st(d[6]));
+      a = pacc(a, PS::st(d[3]));
+      b = pacc(b, PS::st(d[7]));
+      a = pacc(a, PS::st(d[4]));
+      b = pacc(b, PS::st(d[8]));
+      return padd(a, b);
+    } else {
+      P v[9];
 #pragma unroll
-    for (int i = 1; i < 9; ++i) v[i] = PS::ld(PS::st(d[i]));
-    return padd(padd(padd(v[1], v[2]), padd(v[3], v[4])), padd(padd(v[5], v[6]), padd(v[7], v[8])));
+      for (int i = 1; i < 9; ++i) v[i] = PS::ld(PS::st(d[i]));
+      return padd(padd(padd(v[1], v[2]), padd(v[3], v[4])),
+                  padd(padd(v[5], v[6]), padd(v[7], v[8])));
+    }
   }
 
   // rho/psi of this thread's column and of one halo column (lanes 0..3 serve
@@ -706,7 +736,8 @@ struct RowsLoop {
   // Push f*_i of site (o, x) to r + c_i (Ladd bounce-back at Couette walls).
   __device__ __forceinline__ void push(int o, P (&d)[9], P rho, P drho) {
     // 16-bit storages round the rest population stochastically; the bits are
-    // hashed from the site and its relaxed populations (deterministic runs)
+    // hashed from the site and its relaxed populations (deterministic runs),
+    // one hash per site pair
     uint32_t rbits = 0;
     if (sizeof(T2) == 4)
       rbits = mix32(__float_as_uint((float)d[1].x) ^ (__float_as_uint((float)d[6].y) << 7) ^

@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(TTHREADS)
             yd = wrapi(yd, g.ny);
             const int xd = wrapi(x + Q9::cx(i), g.nx);
             dst[lidx(g, s, i, yd, xd)] =
-                i == 0 ? store_sr<STORAGE>(d[s][i], s == 0 ? rbits : mix32(rbits)) : S::st(d[s][i]);
+                i == 0 ? store_sr<STORAGE>(d[s][i], s == 0 ? rbits : __funnelshift_l(rbits, rbits, 16)) : S::st(d[s][i]);
           }
         }
     }
