@@ -73,7 +73,9 @@ struct lb_batch {
   bool dirty = true;
   // distinct physics sets (couplings, tau, rho0, rho_ref) of the replicas,
   // handed to every launch as a PhysTable<float> or PhysTable<double>
-  alignas(16) unsigned char table[sizeof(PhysTable<double>)] = {};
+  alignas(16) unsigned char table[sizeof(PhysTable<double>) > sizeof(PhysTable<float>)
+                                      ? sizeof(PhysTable<double>)
+                                      : sizeof(PhysTable<float>)] = {};
   int nphys = 0;
   bool body = false;  // some replica has a Kolmogorov body-force table
   bool rec = false;   // some replica keeps a shear-response record

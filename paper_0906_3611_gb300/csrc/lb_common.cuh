@@ -101,8 +101,11 @@ struct Phys {
   // FP32 arithmetic: the per-species constants again as adjacent (A, B)
   // pairs, so that packed arithmetic can take them from the parameter space
   // instead of registers: 0..4 Wpsi, 5..7 W2psi, 8 rho_ref, 9 -rho0 E,
-  // 10 omega (one unused pair for FP64, which keeps them in registers)
-  alignas(2 * sizeof(C)) C pr[sizeof(C) == 4 ? 11 : 1][2];
+  // 10 omega, and the collision's products of omega with the D2Q9 weights:
+  // 11 omega w_0, 12 omega w_1, 13 omega w_5, 14 3 omega w_1, 15 4.5 omega w_1,
+  // 16 3 omega w_5, 17 4.5 omega w_5, 18 1 - omega (one unused pair for FP64,
+  // which keeps them in registers)
+  alignas(2 * sizeof(C)) C pr[sizeof(C) == 4 ? 19 : 1][2];
 };
 
 template <typename C>

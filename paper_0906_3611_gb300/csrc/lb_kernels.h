@@ -207,6 +207,15 @@ inline Phys<C> make_phys(const PhysD& d) {
       p.pr[8][s] = p.rho_ref[s];
       p.pr[9][s] = -p.rho0 * p.E[s];  // (as the kernels form it in C)
       p.pr[10][s] = p.omega[s];
+      // the omega-weight products as the kernels would form them in C
+      p.pr[11][s] = p.omega[s] * (C)(4.0 / 9.0);
+      p.pr[12][s] = p.omega[s] * (C)(1.0 / 9.0);
+      p.pr[13][s] = p.omega[s] * (C)(1.0 / 36.0);
+      p.pr[14][s] = p.omega[s] * (C)(3.0 / 9.0);
+      p.pr[15][s] = p.omega[s] * (C)(4.5 / 9.0);
+      p.pr[16][s] = p.omega[s] * (C)(3.0 / 36.0);
+      p.pr[17][s] = p.omega[s] * (C)(4.5 / 36.0);
+      p.pr[18][s] = (C)1 - p.omega[s];
     }
   } else {
     p.pr[0][0] = p.pr[0][1] = C(0);

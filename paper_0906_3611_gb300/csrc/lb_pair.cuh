@@ -62,19 +62,13 @@ __device__ __forceinline__ P pswap(P a) {
 // same result as a conversion followed by an FP32 add, in one instruction per
 // species instead of a conversion per species plus a packed add.
 __device__ __forceinline__ float2 pacc(float2 acc, __half2 v) {
-  const uint32_t u = *reinterpret_cast<const uint32_t*>(&v);
-  asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
-      "add.rn.f32.f16 %0, lo, %0;\n\tadd.rn.f32.f16 %1, hi, %1;\n\t}"
-      : "+f"(acc.x), "+f"(acc.y)
-      : "r"(u));
+  asm("add.rn.f32.f16 %0, %1, %0;" : "+f"(acc.x) : "h"(__half_as_ushort(__low2half(v))));
+  asm("add.rn.f32.f16 %0, %1, %0;" : "+f"(acc.y) : "h"(__half_as_ushort(__high2half(v))));
   return acc;
 }
 __device__ __forceinline__ float2 pacc(float2 acc, __nv_bfloat162 v) {
-  const uint32_t u = *reinterpret_cast<const uint32_t*>(&v);
-  asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
-      "add.rn.f32.bf16 %0, lo, %0;\n\tadd.rn.f32.bf16 %1, hi, %1;\n\t}"
-      : "+f"(acc.x), "+f"(acc.y)
-      : "r"(u));
+  asm("add.rn.f32.bf16 %0, %1, %0;" : "+f"(acc.x) : "h"(__bfloat16_as_ushort(__low2bfloat16(v))));
+  asm("add.rn.f32.bf16 %0, %1, %0;" : "+f"(acc.y) : "h"(__bfloat16_as_ushort(__high2bfloat16(v))));
   return acc;
 }
 

@@ -52,6 +52,7 @@ constexpr int WEXT = 32 + 4;  // a compute warp's row buffer: 32 columns + 2 + 2
 // (hides latency; costs live registers); LAG: carry each row's drho/psi in
 // registers until its collision (else the collision recomputes them from the
 // populations it re-reads: ~13 more instructions, 12 fewer live registers);
+// LAG_BATCH: the same for the batched kernel (its item loop holds more state);
 // CPAR: take the per-species constants (stencil weights, rho_ref, omega) from
 // the parameter space at each use instead of holding them in 22 registers
 // (lets the 16-bit loops run 4 CTAs per SM; costs the FP32 loop 2 %).
@@ -60,22 +61,22 @@ struct RowsCfg;
 template <>
 struct RowsCfg<LB_F64> {
   static constexpr int NCW = 4, SOFF = 2, NSLOT = 5, MINB = 2;  // 16-byte pairs
-  static constexpr bool PIPE = true, LAG = true, CPAR = false;
+  static constexpr bool PIPE = true, LAG = true, LAG_BATCH = true, CPAR = false;
 };
 template <>
 struct RowsCfg<LB_F32> {
   static constexpr int NCW = 4, SOFF = 2, NSLOT = 7, MINB = 3;  // 8-byte pairs
-  static constexpr bool PIPE = true, LAG = true, CPAR = false;
+  static constexpr bool PIPE = true, LAG = true, LAG_BATCH = true, CPAR = false;
 };
 template <>
 struct RowsCfg<LB_BF16_DEV> {
   static constexpr int NCW = 4, SOFF = 4, NSLOT = 8, MINB = 4;  // 4-byte pairs
-  static constexpr bool PIPE = false, LAG = true, CPAR = true;
+  static constexpr bool PIPE = false, LAG = true, LAG_BATCH = false, CPAR = true;
 };
 template <>
 struct RowsCfg<LB_F16_DEV> {
   static constexpr int NCW = 4, SOFF = 4, NSLOT = 8, MINB = 4;
-  static constexpr bool PIPE = false, LAG = true, CPAR = true;
+  static constexpr bool PIPE = false, LAG = true, LAG_BATCH = false, CPAR = true;
 };
 
 template <int STORAGE>
@@ -259,7 +260,7 @@ struct RowsSmem {
 // register slot (k + R) % 5, R = (iteration) % 5, so that the windows slide
 // by renaming registers instead of moving them (the window update is
 // specialised per rotation; staging and collision are shared).
-template <int STORAGE, bool BODY>
+template <int STORAGE, bool BODY, bool LAG = RowsCfg<STORAGE>::LAG>
 struct RowsLoop {
   using PS = PairStore<STORAGE>;
   using T2 = typename PS::T2;
@@ -292,7 +293,7 @@ struct RowsLoop {
   P Wa_, Wb_, Wc_, Wd_, We_, W2c_, W2d_, W2e_, rho_ref_, mrho0E_, om_;  // (unless CPAR)
   static constexpr bool CPAR = RowsCfg<STORAGE>::CPAR;
   __device__ __forceinline__ P cpair(int k) const {  // pair k of the parameter space
-    return *reinterpret_cast<const P*>(ph.pr[k]);
+    return pmk(ph.pr[k][0], ph.pr[k][1]);
   }
   __device__ __forceinline__ P Wa() const { return CPAR ? cpair(0) : Wa_; }
   __device__ __forceinline__ P Wb() const { return CPAR ? cpair(1) : Wb_; }
@@ -305,6 +306,10 @@ struct RowsLoop {
   __device__ __forceinline__ P rho_ref() const { return CPAR ? cpair(8) : rho_ref_; }
   __device__ __forceinline__ P mrho0E() const { return CPAR ? cpair(9) : mrho0E_; }
   __device__ __forceinline__ P om() const { return CPAR ? cpair(10) : om_; }
+  // omega times a weight: k-th precomputed product (CPAR) or formed here
+  __device__ __forceinline__ P omw(int k, C w) const {
+    return CPAR ? cpair(11 + k) : pmul(om_, pbc(w));
+  }
   // windows (see above) and loop state
   P Sx[5], Sy[5], Cx[5], Cy[5], lag_drho[5], lag_psi[5];
   int bad;
@@ -391,24 +396,31 @@ struct RowsLoop {
   }
   // sum of the nine staged populations of a site: a pairwise tree for the
   // 32/64-bit storages; two chains of mixed-precision adds for the 16-bit ones
-  // (no separate conversion of each value)
-  static __device__ __forceinline__ P staged_sum9(const T2* p) {
+  // (no separate conversion of each value).  The collision's recomputation
+  // (LAG off) repeats it bit for bit from the same staged values.
+  static __device__ __forceinline__ P raw_sum9(const T2 (&r)[9]) {
     if constexpr (sizeof(T2) == 4) {
-      P a = PS::ld(p[0]), b = PS::ld(p[5 * SW]);
-      a = pacc(a, p[1 * SW]);
-      b = pacc(b, p[6 * SW]);
-      a = pacc(a, p[2 * SW]);
-      b = pacc(b, p[7 * SW]);
-      a = pacc(a, p[3 * SW]);
-      b = pacc(b, p[8 * SW]);
-      a = pacc(a, p[4 * SW]);
+      P a = PS::ld(r[0]), b = PS::ld(r[5]);
+      a = pacc(a, r[1]);
+      b = pacc(b, r[6]);
+      a = pacc(a, r[2]);
+      b = pacc(b, r[7]);
+      a = pacc(a, r[3]);
+      b = pacc(b, r[8]);
+      a = pacc(a, r[4]);
       return padd(a, b);
     } else {
       P v[9];
 #pragma unroll
-      for (int i = 0; i < 9; ++i) v[i] = PS::ld(p[i * SW]);
+      for (int i = 0; i < 9; ++i) v[i] = PS::ld(r[i]);
       return sum9(v);
     }
+  }
+  static __device__ __forceinline__ P staged_sum9(const T2* p) {
+    T2 r[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) r[i] = p[i * SW];
+    return raw_sum9(r);
   }
   // pairwise sum of a site's nine populations (a shorter dependency chain than
   // a running sum; the collision repeats it bit for bit)
@@ -456,7 +468,7 @@ struct RowsLoop {
     Cx[k3] = X1;
     Cy[k1] = padd(Cy[k1], K);
     Cy[k3] = psub(pbc(C(0)), K);
-    if (RowsCfg<STORAGE>::LAG) {
+    if (LAG) {
       lag_drho[k2] = my_drho;
       lag_psi[k2] = my_psi;
     }
@@ -671,10 +683,14 @@ struct RowsLoop {
   // for the rounded storages); rho is the site's density pair.
   __device__ __forceinline__ void relax(const T2* orow, P Sx0, P Sy0, P Cx0, P Cy0, P& drho,
                                         P psi0, C gb, P (&d)[9], P& rho_out, C& ux_out) {
+    T2 raw[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) d[i] = PS::ld(orow[i * SW]);
-    if (!RowsCfg<STORAGE>::LAG) {  // the row's drho and psi, as its staging formed them
-      drho = sum9(d);
+    for (int i = 0; i < 9; ++i) {
+      raw[i] = orow[i * SW];
+      d[i] = PS::ld(raw[i]);
+    }
+    if (!LAG) {  // the row's drho and psi, as its staging formed them
+      drho = raw_sum9(raw);
       psi0 = psi_of(drho);
     }
     const P rho = padd(rho_ref(), drho);
@@ -700,16 +716,16 @@ struct RowsLoop {
     const P vy = pfma(k, Gy, pbc(uy));
     // BGK relaxation toward the shifted equilibrium (factored form, see lb_site.cuh)
     {
-      const P keep = psub(pbc(C(1)), om());
+      const P keep = CPAR ? cpair(18) : psub(pbc(C(1)), om());
       const P v2 = pfma(vx, vx, pmul(vy, vy));
       const P tt = pfma(pmul(pbc(C(-1.5)), rho), v2, drho);
-      const P B0 = pmul(pmul(om(), pbc(wq<C>(0))), tt);
-      const P B1 = pmul(pmul(om(), pbc(wq<C>(1))), tt);
-      const P B2 = pmul(pmul(om(), pbc(wq<C>(5))), tt);
-      const P a1 = pmul(pmul(om(), pbc(C(3) * wq<C>(1))), rho);
-      const P b1 = pmul(pmul(om(), pbc(C(4.5) * wq<C>(1))), rho);
-      const P a2 = pmul(pmul(om(), pbc(C(3) * wq<C>(5))), rho);
-      const P b2 = pmul(pmul(om(), pbc(C(4.5) * wq<C>(5))), rho);
+      const P B0 = pmul(omw(0, wq<C>(0)), tt);
+      const P B1 = pmul(omw(1, wq<C>(1)), tt);
+      const P B2 = pmul(omw(2, wq<C>(5)), tt);
+      const P a1 = pmul(omw(3, C(3) * wq<C>(1)), rho);
+      const P b1 = pmul(omw(4, C(4.5) * wq<C>(1)), rho);
+      const P a2 = pmul(omw(5, C(3) * wq<C>(5)), rho);
+      const P b2 = pmul(omw(6, C(4.5) * wq<C>(5)), rho);
       d[0] = pfma(keep, d[0], B0);
       const P ex = pfma(pmul(b1, vx), vx, B1), ax = pmul(a1, vx);
       const P ey = pfma(pmul(b1, vy), vy, B1), ay = pmul(a1, vy);
@@ -792,7 +808,7 @@ struct RowsLoop {
 // next staged row in the CTA's slot ring (identical in every thread); on
 // entry every slot is free or will be released by the compute warps.  A
 // bounded wait that gives up raises *s_abort (read it after a __syncthreads).
-template <int STORAGE, bool BODY>
+template <int STORAGE, bool BODY, bool LAG = RowsCfg<STORAGE>::LAG>
 __device__ __forceinline__ void rows_range(
     const typename PairStore<STORAGE>::T2* __restrict__ src,
     typename PairStore<STORAGE>::T2* __restrict__ dst, const Geom& g,
@@ -800,8 +816,8 @@ __device__ __forceinline__ void rows_range(
     const typename Store<STORAGE>::C* body, int x0, int x1, int ylo, int yhi,
     const RowsSmem<STORAGE>& sm, int& ring, int* s_abort, Status* status, int& bad,
     const Series& sr) {
-  RowsLoop<STORAGE, BODY> L(src, dst, g, ph, Uwall, body, x0, x1, ylo, yhi, sm, ring, s_abort,
-                            status, sr);
+  RowsLoop<STORAGE, BODY, LAG> L(src, dst, g, ph, Uwall, body, x0, x1, ylo, yhi, sm, ring,
+                                 s_abort, status, sr);
   if (L.warp == RowsCfg<STORAGE>::NCW)
     L.produce();
   else

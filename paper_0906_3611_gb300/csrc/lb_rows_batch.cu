@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(cta_threads<STORAGE>(), RowsCfg<STORAGE>::MINB
     __syncthreads();
     if (s_skip) continue;
     const Series none{};
-    rows_range<STORAGE, (MODE > 0)>(s_src, s_dst, s_g, tab.p[ONE ? 0 : s_phys], s_U, s_body,
+    rows_range<STORAGE, (MODE > 0), RowsCfg<STORAGE>::LAG_BATCH>(s_src, s_dst, s_g, tab.p[ONE ? 0 : s_phys], s_U, s_body,
                                     s_item.x0, s_item.x1, s_item.ylo, s_item.yhi, sm, ring,
                                     &s_abort, status, bad, MODE == 2 ? s_sr : none);
     __syncthreads();
