@@ -224,7 +224,12 @@ LB_API int64_t lb_time(const lb_handle *h);
 
 /* Read and clear the device status word; synchronises.  Returns LB_OK,
  * LB_ENEGRHO (a density <= 0 was met: the velocity shift of that species was
- * skipped there), or LB_ETIMEOUT. */
+ * skipped there), or LB_ETIMEOUT (a bounded wait of the row-streaming kernel
+ * for a staged row gave up -- about a second by default -- and the step was
+ * abandoned: the state is then undefined until lb_set_state or
+ * lb_init_random).  Test hook: the environment variable LB_TEST_WAIT_CYCLES,
+ * read by lb_create / lb_batch_create, shortens that bound to the given
+ * number of SM cycles, so that the timeout path can be exercised. */
 LB_API int lb_status(lb_handle *h);
 
 /* Wait for all work enqueued by this handle. */

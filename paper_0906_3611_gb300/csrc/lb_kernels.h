@@ -6,6 +6,7 @@
 #include <math.h>
 #include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include "lb_common.cuh"
 
@@ -27,6 +28,19 @@ struct PhysD {
   int kk;     // its wave number
   int dev;  // 1 for the deviation storages (every storage but FP64)
 };
+
+// Bound (SM cycles) of the row kernels' waits for a staged row: the default,
+// or LB_TEST_WAIT_CYCLES from the environment (read when a handle or batch is
+// created; a test hook that shortens the bound so that a wait gives up and
+// the timeout path runs -- the step then reports LB_ETIMEOUT).
+inline long long wait_limit_from_env(long long dflt) {
+  const char* v = getenv("LB_TEST_WAIT_CYCLES");
+  if (!v || !*v) return dflt;
+  char* end = nullptr;
+  const long long c = strtoll(v, &end, 10);
+  if (end == v || c < 0) return dflt;
+  return c < dflt ? c : dflt;
+}
 
 // Checks of the physics part of lb_params shared by every entry point that
 // takes one: tau_s > 1/2, rho0 > 0, a known boundary and storage, a Kolmogorov

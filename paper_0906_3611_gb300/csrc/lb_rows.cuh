@@ -32,8 +32,11 @@
 // population is read from DRAM once and written once; the halos (SOFF
 // columns, 2+2 rows per range) are served by L2.
 //
-// Every mbarrier wait is bounded: on timeout the kernel sets the status word,
-// raises the CTA's abort flag, drains its own copies (bounded) and leaves.
+// Every mbarrier wait is bounded and taken by whole warps that decide together
+// (so a warp leaves a wait converged): on timeout the kernel sets the status
+// word, raises the CTA's abort flag, drains its own copies (bounded) and
+// leaves.  The bound of the compute warps' waits is a launch parameter (the
+// library's default ~2^31 cycles; a test hook shrinks it to exercise this path).
 #pragma once
 
 #include "lb_pair.cuh"
@@ -166,27 +169,55 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return done != 0;
 }
-// Bounded wait: gives up after ~2^31 cycles (about a second).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > (1LL << 31)) return false;
-  }
-  return true;
+// Non-blocking test of a phase (try_wait may suspend the thread for a while
+// before it reports an incomplete phase; test_wait answers at once).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
 }
-// Bounded wait with exponential sleep between polls, for a waiter that is far
-// ahead of the event (the staging warp): it then takes few issue slots.
-__device__ __forceinline__ bool mbar_wait_backoff(uint64_t* bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
+
+// Bounded wait of a whole converged warp: every lane polls, and the lanes
+// decide together (warp votes) whether the phase completed or the bound ran
+// out, so the warp leaves the wait converged whatever the outcome.  With a
+// bound shorter than the default (the test hook) the polls do not suspend, so
+// that the bound is what ends the wait.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit) {
+  if (limit < kWaitLimitDefault) {
+    const long long t0 = clock64();
+    while (true) {
+      if (__all_sync(0xffffffffu, mbar_test_wait(bar, parity))) return true;
+      if (__any_sync(0xffffffffu, clock64() - t0 > limit)) return false;
+    }
+  }
+  if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+  const long long t0 = clock64();
+  while (true) {
+    if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+    if (__any_sync(0xffffffffu, clock64() - t0 > limit)) return false;
+  }
+}
+// The same with exponential sleep between polls, for a waiter that is far
+// ahead of the event (the staging warp): it then takes few issue slots.  It
+// also gives up as soon as the CTA's abort flag is raised.
+__device__ __forceinline__ bool mbar_wait_backoff(uint64_t* bar, uint32_t parity,
+                                                  const int* s_abort) {
+  if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
   const long long t0 = clock64();
   unsigned ns = 32;
-  while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > (1LL << 31)) return false;
+  while (true) {
+    if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+    if (__any_sync(0xffffffffu, clock64() - t0 > kWaitLimitDefault || *(volatile const int*)s_abort))
+      return false;
     __nanosleep(ns);
     if (ns < 512) ns *= 2;
   }
-  return true;
 }
 __device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, uint32_t bytes,
                                          uint64_t* bar) {
@@ -279,9 +310,11 @@ struct RowsLoop {
   int* s_abort;
   Status* status;
   int x0, ylo, nstage, ring;
+  int issued = 0;  // rows the staging warp has issued (staging warp only)
   C Uwall;
   const C* body;     // Kolmogorov body acceleration per row (BODY only; nullptr: none)
   const Series& sr;  // shear-response record (sr.buf == nullptr: off)
+  long long wait_limit;  // bound of the compute warps' waits for a staged row (cycles)
   C sacc;            // this thread's sum of u_x sin(k y) over its collided sites
   const C* swt;      // the record's row weights (nullptr: no record), kept in registers
   // this thread (a compute thread serves column x = x0 + t)
@@ -318,10 +351,10 @@ struct RowsLoop {
                                       const Geom& g_, const Phys<C>& ph_, C Uwall_,
                                       const C* body_, int x0_, int x1, int ylo_, int yhi,
                                       const RowsSmem<STORAGE>& sm_, int ring_, int* s_abort_,
-                                      Status* status_, const Series& sr_)
+                                      Status* status_, const Series& sr_, long long wait_limit_)
       : src(src_), g(g_), ph(ph_), sm(sm_), s_abort(s_abort_), status(status_), x0(x0_),
         ylo(ylo_), nstage((yhi - ylo_) + 4), ring(ring_), Uwall(Uwall_), body(body_), sr(sr_),
-        sacc(C(0)), swt(sr_.buf ? (const C*)sr_.wt : nullptr) {
+        wait_limit(wait_limit_), sacc(C(0)), swt(sr_.buf ? (const C*)sr_.wt : nullptr) {
     warp = threadIdx.x >> 5;
     lane = threadIdx.x & 31;
     t = (warp < NCW) ? (int)threadIdx.x : 0;
@@ -365,7 +398,7 @@ struct RowsLoop {
     for (; j < nstage; ++j) {
       const int s = slot_of(j);
       const uint32_t rnd = round_of(j);
-      if (rnd > 0 && !mbar_wait_backoff(&sm.empty[s], (rnd - 1) & 1)) {
+      if (rnd > 0 && !mbar_wait_backoff(&sm.empty[s], (rnd - 1) & 1, s_abort)) {
         if (lane == 0) {
           atomicExch(&status->timeout, 1u);
           *s_abort = 1;
@@ -375,14 +408,19 @@ struct RowsLoop {
       if (*(volatile int*)s_abort) break;
       issue_row<STORAGE>(src, sm.stage + s * SLOT, &sm.full[s], g, x0, ylo - 2 + j, lane);
     }
-    // on abort, wait (bounded) for the copies in flight, so that none is still
-    // writing into this CTA's shared memory when it moves on or exits
-    if (j < nstage && lane == 0) {
-      for (int k = (j > NSLOT ? j - NSLOT : 0); k < j; ++k) {
-        const long long t0 = clock64();
-        while (!mbar_try_wait(&sm.full[slot_of(k)], round_of(k) & 1)) {
-          if (clock64() - t0 > (1LL << 31)) break;
-        }
+    issued = j;
+  }
+
+  // After an abort (called by one thread of the staging warp, once every warp
+  // of the CTA has left the range): wait, bounded, for the copies still in
+  // flight, so that none is writing into this CTA's shared memory when it
+  // moves on or exits.  Only the last NSLOT issued rows can be outstanding: a
+  // slot is refilled only after its previous row was consumed.
+  __device__ __forceinline__ void drain() const {
+    for (int k = (issued > NSLOT ? issued - NSLOT : 0); k < issued; ++k) {
+      const long long t0 = clock64();
+      while (!mbar_try_wait(&sm.full[slot_of(k)], round_of(k) & 1)) {
+        if (clock64() - t0 > kWaitLimitDefault) break;
       }
     }
   }
@@ -540,7 +578,7 @@ struct RowsLoop {
   }
 
   __device__ __forceinline__ bool wait_row(int j) {
-    if (!mbar_wait_bounded(&sm.full[slot_of(j)], round_of(j) & 1)) {
+    if (!mbar_wait_bounded(&sm.full[slot_of(j)], round_of(j) & 1, wait_limit)) {
       if (lane == 0) {
         atomicExch(&status->timeout, 1u);
         *s_abort = 1;
@@ -807,7 +845,8 @@ struct RowsLoop {
 // ylo .. yhi-1 of the lattice (src -> dst).  `ring` is the position of the
 // next staged row in the CTA's slot ring (identical in every thread); on
 // entry every slot is free or will be released by the compute warps.  A
-// bounded wait that gives up raises *s_abort (read it after a __syncthreads).
+// bounded wait that gives up raises *s_abort (read it after a __syncthreads);
+// every thread of the CTA calls this (it ends with a CTA barrier).
 template <int STORAGE, bool BODY, bool LAG = RowsCfg<STORAGE>::LAG>
 __device__ __forceinline__ void rows_range(
     const typename PairStore<STORAGE>::T2* __restrict__ src,
@@ -815,13 +854,17 @@ __device__ __forceinline__ void rows_range(
     const Phys<typename Store<STORAGE>::C>& ph, typename Store<STORAGE>::C Uwall,
     const typename Store<STORAGE>::C* body, int x0, int x1, int ylo, int yhi,
     const RowsSmem<STORAGE>& sm, int& ring, int* s_abort, Status* status, int& bad,
-    const Series& sr) {
+    const Series& sr, long long wait_limit) {
   RowsLoop<STORAGE, BODY, LAG> L(src, dst, g, ph, Uwall, body, x0, x1, ylo, yhi, sm, ring,
-                                 s_abort, status, sr);
+                                 s_abort, status, sr, wait_limit);
   if (L.warp == RowsCfg<STORAGE>::NCW)
     L.produce();
   else
     L.consume();
+  // every warp has left the range: after an abort the staging warp waits for
+  // the copies it issued that may still be landing
+  __syncthreads();
+  if (*(volatile int*)s_abort && L.warp == RowsCfg<STORAGE>::NCW && L.lane == 0) L.drain();
   bad += L.bad;
   ring += L.nstage;
 }
