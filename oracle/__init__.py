@@ -74,6 +74,17 @@ def _load():
         lib.lbo_shear_diagnostics.restype = ctypes.c_long
         lib.lbo_phi_overlap.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, dp]
         lib.lbo_phi_overlap.restype = None
+        lib.lbo_densities_ns.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
+        lib.lbo_densities_ns.restype = None
+        lib.lbo_forces_ns.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, dp]
+        lib.lbo_forces_ns.restype = None
+        lib.lbo_step_ns.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_long, ctypes.c_int]
+        lib.lbo_step_ns.restype = ctypes.c_long
+        lib.lbo_observables_ns.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, dp, dp]
+        lib.lbo_observables_ns.restype = ctypes.c_long
+        lib.lbo_init_ns.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                    dp, dp]
+        lib.lbo_init_ns.restype = None
         lib.lbo_max_threads.argtypes = []
         lib.lbo_max_threads.restype = ctypes.c_int
         _lib = lib
@@ -216,6 +227,79 @@ def init_densities(nx: int, ny: int, seed: int, kind: int, init) -> np.ndarray:
     iv[: len(init)] = init
     lib.lbo_init_densities(nx, ny, ctypes.c_uint64(seed), int(kind), _dp(iv), _dp(rho))
     return rho
+
+
+# ---- N_s species (Sec. II, Eq. (be) and Eq. (FORCE) for s = 1..N_s) ----
+
+def params_ns(p: dict) -> np.ndarray:
+    """Parameter vector of the N_s-species passes.  Keys: ns, tau (ns values),
+    rho0, Ga, Gr (ns values each), G (ns x ns symmetric cross couplings; the
+    diagonal is not used), boundary, U_wall, g_kolmo, k_kolmo."""
+    ns = int(p["ns"])
+    tau = np.asarray(p.get("tau", [1.0] * ns), dtype=np.float64)
+    Ga = np.asarray(p.get("Ga", [0.0] * ns), dtype=np.float64)
+    Gr = np.asarray(p.get("Gr", [0.0] * ns), dtype=np.float64)
+    G = np.asarray(p.get("G", np.zeros((ns, ns))), dtype=np.float64).reshape(ns, ns)
+    head = [float(ns), p.get("rho0", 1.0), float(p.get("boundary", PERIODIC)), p.get("U_wall", 0.0),
+            p.get("g_kolmo", 0.0), float(p.get("k_kolmo", 1))]
+    return np.concatenate([np.array(head), tau, Ga, Gr, G.ravel()])
+
+
+def densities_ns(f: np.ndarray) -> np.ndarray:
+    """rho[ns, ny, nx] of f[ns, 9, ny, nx]."""
+    lib = _load()
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    ns, _, ny, nx = f.shape
+    rho = np.empty((ns, ny, nx))
+    lib.lbo_densities_ns(_dp(f), ns, nx, ny, _dp(rho))
+    return rho
+
+
+def forces_ns(rho: np.ndarray, p: dict) -> np.ndarray:
+    """F[ns, 2, ny, nx] of density fields rho[ns, ny, nx], Eq. (FORCE) for N_s species."""
+    lib = _load()
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    ns, ny, nx = rho.shape
+    assert ns == int(p["ns"])
+    F = np.empty((ns, 2, ny, nx))
+    lib.lbo_forces_ns(_dp(rho), nx, ny, _dp(params_ns(p)), _dp(F))
+    return F
+
+
+def step_ns(f: np.ndarray, p: dict, nsteps: int = 1, threads: int = 0):
+    """Advance a copy of f[ns, 9, ny, nx] by nsteps; returns (f_new, bad_count)."""
+    lib = _load()
+    g = np.array(f, dtype=np.float64, order="C", copy=True)
+    ns, _, ny, nx = g.shape
+    assert ns == int(p["ns"])
+    bad = lib.lbo_step_ns(_dp(g), nx, ny, _dp(params_ns(p)), int(nsteps), int(threads))
+    if bad < 0:
+        raise MemoryError("oracle step_ns: allocation failed or ns out of range")
+    return g, int(bad)
+
+
+def observables_ns(f: np.ndarray, p: dict) -> dict:
+    """mass[ns] (per species), momentum[2], stress[3] and the bad count of a state."""
+    lib = _load()
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    ns, _, ny, nx = f.shape
+    stress = np.empty(3)
+    mass = np.empty(ns + 2)
+    bad = lib.lbo_observables_ns(_dp(f), nx, ny, _dp(params_ns(p)), _dp(stress), _dp(mass))
+    if bad < 0:
+        raise MemoryError("oracle observables_ns: allocation failed")
+    return {"mass": mass[:ns], "momentum": mass[ns:], "stress": stress, "bad": int(bad)}
+
+
+def init_ns(ns: int, nx: int, ny: int, seed: int, mean, amp) -> np.ndarray:
+    """Seeded state at rest: rho_s = mean[s] + amp[s] (2u - 1), one Philox block
+    (counter (site, 1 + s), key seed) per site and species, f = w_i rho_s."""
+    lib = _load()
+    f = np.empty((ns, 9, ny, nx))
+    m = np.ascontiguousarray(mean, dtype=np.float64)
+    a = np.ascontiguousarray(amp, dtype=np.float64)
+    lib.lbo_init_ns(_dp(f), ns, nx, ny, ctypes.c_uint64(seed), _dp(m), _dp(a))
+    return f
 
 
 def max_threads() -> int:

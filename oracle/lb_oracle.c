@@ -538,3 +538,299 @@ void lbo_init(double *f, int nx, int ny, uint64_t seed, int kind, const double *
         f[((size_t)(s * 9 + i)) * N + site] = w9(i) * rho[s * N + site];
   free(rho);
 }
+
+/* ======================================================================
+ * N_s species (Sec. II: Eq. (be) and Eq. (FORCE) are written for species
+ * s = 1..N_s with a symmetric cross-coupling matrix G_ss', s' != s).  The
+ * same whole-lattice passes as above, for any number of species ns >= 1.
+ *
+ * Layout: f[((s*9 + i)*ny + y)*nx + x], s = 0..ns-1.
+ * Parameter vector q[] (doubles):
+ *   0 ns   1 rho0   2 boundary (0 periodic, 1 Couette)   3 U_wall
+ *   4 g (Kolmogorov amplitude)   5 k (its wave number)
+ *   6 .. 6+ns-1          tau_s
+ *   6+ns .. 6+2ns-1      Ga_s   (G^a_s: belt 1, weights w)
+ *   6+2ns .. 6+3ns-1     Gr_s   (G^r_s: belts 1 and 2, weights p)
+ *   6+3ns .. 6+3ns+ns^2-1  G[s][s'] row-major (symmetric; diagonal unused)
+ *
+ *   F^X_s = -(1/rho0^2) rho_s(r) sum_{s' != s} G_ss' sum_{j in belt 1} w_j rho_s'(r + c_j) c_j
+ * taken as a sum over s' (in increasing order) of the per-pair terms, so
+ * that with ns = 2 every term is the two-species pass's own expression.
+ * ====================================================================== */
+#define QNS(q) ((int)(q)[0])
+#define QTAU(q, s) ((q)[6 + (s)])
+#define QGA(q, s) ((q)[6 + QNS(q) + (s)])
+#define QGR(q, s) ((q)[6 + 2 * QNS(q) + (s)])
+#define QG(q, s, t) ((q)[6 + 3 * QNS(q) + (s) * QNS(q) + (t)])
+
+static inline size_t IDXN(int s, int i, int y, int x, int nx, int ny) {
+  return (((size_t)(s * 9 + i) * (size_t)ny + (size_t)y) * (size_t)nx) + (size_t)x;
+}
+
+/* pass 1: rho[s][y][x] = sum_i f_is */
+void lbo_densities_ns(const double *f, int ns, int nx, int ny, double *rho) {
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < ny; ++y)
+    for (int s = 0; s < ns; ++s)
+      for (int x = 0; x < nx; ++x) {
+        double r = 0.0;
+        for (int i = 0; i < 9; ++i) r += f[IDXN(s, i, y, x, nx, ny)];
+        rho[((size_t)s * ny + y) * nx + x] = r;
+      }
+}
+
+/* passes 2-3: psi of Eq. (PSI) and the forces of Eq. (FORCE); F[s][comp][y][x] */
+void lbo_forces_ns(const double *rho, int nx, int ny, const double *q, double *F) {
+  const int ns = QNS(q);
+  const double rho0 = q[1];
+  const int couette = (int)q[2];
+  const size_t N = (size_t)nx * ny;
+  double *psi = (double *)malloc((size_t)ns * N * sizeof(double));
+  if (!psi) return;
+  for (size_t k = 0; k < (size_t)ns * N; ++k) psi[k] = psi_of(rho[k], rho0);
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < ny; ++y) {
+    double sxx[16], sxy[16]; /* belt-1 sums of the other species' densities (ns <= 16) */
+    const double body = q[4] * sin(2.0 * M_PI * q[5] * (double)y / (double)ny);
+    for (int s = 0; s < ns; ++s) {
+      const double Ga = QGA(q, s), Gr = QGR(q, s);
+      for (int x = 0; x < nx; ++x) {
+        double sa_x = 0, sa_y = 0, sr_x = 0, sr_y = 0;
+        for (int t = 0; t < ns; ++t) sxx[t] = sxy[t] = 0.0;
+        for (int j = 1; j < 25; ++j) {
+          const int yy = stencil_row(y + CYF[j], ny, couette);
+          const int xx = wrap(x + CXF[j], nx);
+          const double ps = psi[((size_t)s * ny + yy) * nx + xx];
+          sa_x += wF(j) * ps * CXF[j];
+          sa_y += wF(j) * ps * CYF[j];
+          sr_x += pF(j) * ps * CXF[j];
+          sr_y += pF(j) * ps * CYF[j];
+          for (int t = 0; t < ns; ++t) {
+            if (t == s) continue;
+            const double ro = rho[((size_t)t * ny + yy) * nx + xx];
+            sxx[t] += wF(j) * ro * CXF[j];
+            sxy[t] += wF(j) * ro * CYF[j];
+          }
+        }
+        const double pc = psi[((size_t)s * ny + y) * nx + x];
+        const double rc = rho[((size_t)s * ny + y) * nx + x];
+        const double Fa_x = -Ga * pc * sa_x, Fa_y = -Ga * pc * sa_y;
+        const double Fr_x = -Gr * pc * sr_x, Fr_y = -Gr * pc * sr_y;
+        double Fx_x = 0.0, Fx_y = 0.0;
+        int first = 1;
+        for (int t = 0; t < ns; ++t) {
+          if (t == s) continue;
+          const double G = QG(q, s, t);
+          const double tx = -(G / (rho0 * rho0)) * rc * sxx[t];
+          const double ty = -(G / (rho0 * rho0)) * rc * sxy[t];
+          if (first) {
+            Fx_x = tx;
+            Fx_y = ty;
+            first = 0;
+          } else {
+            Fx_x += tx;
+            Fx_y += ty;
+          }
+        }
+        const double Fb_x = rc * body;
+        F[(((size_t)s * 2 + 0) * ny + y) * nx + x] = Fa_x + Fr_x + Fx_x + Fb_x;
+        F[(((size_t)s * 2 + 1) * ny + y) * nx + x] = Fa_y + Fr_y + Fx_y;
+      }
+    }
+  }
+  free(psi);
+}
+
+/* moments, common velocity u = sum_s j_s/tau_s / sum_s rho_s/tau_s and the
+ * shifted velocities v_s = u + tau_s F_s / rho_s (no shift where rho_s <= 0,
+ * counted) */
+static long macro_state_ns(const double *f, int nx, int ny, const double *q, double *rho,
+                           double *F, double *v) {
+  const int ns = QNS(q);
+  const size_t N = (size_t)nx * ny;
+  lbo_densities_ns(f, ns, nx, ny, rho);
+  lbo_forces_ns(rho, nx, ny, q, F);
+  long bad = 0;
+#pragma omp parallel for schedule(static) reduction(+ : bad)
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      const size_t r = (size_t)y * nx + x;
+      double den = 0.0, nux = 0.0, nuy = 0.0;
+      for (int s = 0; s < ns; ++s) {
+        double jx = 0.0, jy = 0.0;
+        for (int i = 0; i < 9; ++i) {
+          jx += f[IDXN(s, i, y, x, nx, ny)] * CX9[i];
+          jy += f[IDXN(s, i, y, x, nx, ny)] * CY9[i];
+        }
+        const double ts = QTAU(q, s);
+        if (s == 0) {
+          den = rho[r] / ts;
+          nux = jx / ts;
+          nuy = jy / ts;
+        } else {
+          den += rho[s * N + r] / ts;
+          nux += jx / ts;
+          nuy += jy / ts;
+        }
+      }
+      const double ux = nux / den, uy = nuy / den;
+      for (int s = 0; s < ns; ++s) {
+        const double ts = QTAU(q, s);
+        const double rs = rho[s * N + r];
+        double sx = 0.0, sy = 0.0;
+        if (rs > 0.0) {
+          sx = ts * F[(s * 2 + 0) * N + r] / rs;
+          sy = ts * F[(s * 2 + 1) * N + r] / rs;
+        } else {
+          ++bad;
+        }
+        v[(s * 2 + 0) * N + r] = ux + sx;
+        v[(s * 2 + 1) * N + r] = uy + sy;
+      }
+    }
+  return bad;
+}
+
+/* one step f -> fn: BGK toward the shifted equilibrium (Eq. (be)), then
+ * streaming with halfway bounce-back at moving walls */
+static long one_step_ns(const double *f, double *fn, int nx, int ny, const double *q,
+                        double *rho, double *F, double *v, double *fpost) {
+  const int ns = QNS(q);
+  const size_t N = (size_t)nx * ny;
+  const int couette = (int)q[2];
+  const double U = q[3];
+  long bad = macro_state_ns(f, nx, ny, q, rho, F, v);
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < ny; ++y)
+    for (int s = 0; s < ns; ++s) {
+      const double ts = QTAU(q, s);
+      for (int x = 0; x < nx; ++x) {
+        const size_t r = (size_t)y * nx + x;
+        const double rs = rho[s * N + r];
+        const double vx = v[(s * 2 + 0) * N + r], vy = v[(s * 2 + 1) * N + r];
+        for (int i = 0; i < 9; ++i) {
+          const size_t k = IDXN(s, i, y, x, nx, ny);
+          fpost[k] = f[k] - (f[k] - feq(i, rs, vx, vy)) / ts;
+        }
+      }
+    }
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < ny; ++y)
+    for (int s = 0; s < ns; ++s)
+      for (int i = 0; i < 9; ++i)
+        for (int x = 0; x < nx; ++x) {
+          const double val = fpost[IDXN(s, i, y, x, nx, ny)];
+          const int yd = y + CY9[i];
+          if (couette && (yd < 0 || yd >= ny)) {
+            const double Uw = (yd >= ny) ? U : -U;
+            const double rs = rho[s * N + (size_t)y * nx + x];
+            fn[IDXN(s, OPP9[i], y, x, nx, ny)] = val - 2.0 * w9(i) * rs * (CX9[i] * Uw) / CS2;
+          } else {
+            fn[IDXN(s, i, wrap(yd, ny), wrap(x + CX9[i], nx), nx, ny)] = val;
+          }
+        }
+  return bad;
+}
+
+/* Advance f (in place) by nsteps; returns the bad-density count or -1. */
+long lbo_step_ns(double *f, int nx, int ny, const double *q, long nsteps, int nthreads) {
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+  const int ns = QNS(q);
+  if (ns < 1 || ns > 16) return -1;
+  const size_t N = (size_t)nx * ny;
+  double *fn = (double *)malloc((size_t)ns * 9 * N * sizeof(double));
+  double *fpost = (double *)malloc((size_t)ns * 9 * N * sizeof(double));
+  double *rho = (double *)malloc((size_t)ns * N * sizeof(double));
+  double *F = (double *)malloc((size_t)ns * 2 * N * sizeof(double));
+  double *v = (double *)malloc((size_t)ns * 2 * N * sizeof(double));
+  if (!fn || !fpost || !rho || !F || !v) {
+    free(fn); free(fpost); free(rho); free(F); free(v);
+    return -1;
+  }
+  long bad = 0;
+  for (long t = 0; t < nsteps; ++t) {
+    bad += one_step_ns(f, fn, nx, ny, q, rho, F, v, fpost);
+    memcpy(f, fn, (size_t)ns * 9 * N * sizeof(double));
+  }
+  free(fn); free(fpost); free(rho); free(F); free(v);
+  return bad;
+}
+
+/* Observables of an ns-species state: mass[ns + 2] = {M_0 .. M_{ns-1}, P_x, P_y}
+ * (P = sum_s sum_i f_is c_i), stress[3] = {mean sigma_xy, wall_top,
+ * wall_bottom} as for two species.  Returns the bad-density count or -1. */
+long lbo_observables_ns(const double *f, int nx, int ny, const double *q, double *stress,
+                        double *mass) {
+  const int ns = QNS(q);
+  const size_t N = (size_t)nx * ny;
+  const int couette = (int)q[2];
+  const double U = q[3];
+  double *rho = (double *)malloc((size_t)ns * N * sizeof(double));
+  double *F = (double *)malloc((size_t)ns * 2 * N * sizeof(double));
+  double *v = (double *)malloc((size_t)ns * 2 * N * sizeof(double));
+  if (!rho || !F || !v) {
+    free(rho); free(F); free(v);
+    return -1;
+  }
+  long bad = macro_state_ns(f, nx, ny, q, rho, F, v);
+  double Px = 0, Py = 0, sxy = 0, wt = 0, wb = 0;
+  for (int s = 0; s < ns; ++s) mass[s] = 0.0;
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      const size_t r = (size_t)y * nx + x;
+      for (int s = 0; s < ns; ++s) {
+        const double ts = QTAU(q, s);
+        const double rs = rho[s * N + r];
+        const double vx = v[(s * 2 + 0) * N + r], vy = v[(s * 2 + 1) * N + r];
+        double neq_xy = 0.0;
+        for (int i = 0; i < 9; ++i) {
+          const double fi = f[IDXN(s, i, y, x, nx, ny)];
+          Px += fi * CX9[i];
+          Py += fi * CY9[i];
+          neq_xy += (fi - feq(i, rs, vx, vy)) * CX9[i] * CY9[i];
+          if (couette && (y + CY9[i] < 0 || y + CY9[i] >= ny)) {
+            const double fp = fi - (fi - feq(i, rs, vx, vy)) / ts;
+            const int top = (y + CY9[i] >= ny);
+            const double Uw = top ? U : -U;
+            const double back = fp - 2.0 * w9(i) * rs * (CX9[i] * Uw) / CS2;
+            const double push = CX9[i] * (fp + back);
+            if (top) wt -= push; else wb += push;
+          }
+        }
+        sxy -= (1.0 - 1.0 / (2.0 * ts)) * neq_xy;
+        mass[s] += rs;
+      }
+    }
+  mass[ns] = Px;
+  mass[ns + 1] = Py;
+  if (stress) {
+    stress[0] = sxy / (double)N;
+    stress[1] = couette ? wt / nx : 0.0;
+    stress[2] = couette ? wb / nx : 0.0;
+  }
+  free(rho); free(F); free(v);
+  return bad;
+}
+
+/* Seeded ns-species initial state at rest: species s of site r draws one
+ * Philox4x32-10 block with counter (r_lo, r_hi, 1 + s, 0) and key (seed),
+ * u = word_0 * 2^-32, rho_s = mean[s] + amp[s] (2u - 1), f_is = w_i rho_s. */
+void lbo_init_ns(double *f, int ns, int nx, int ny, uint64_t seed, const double *mean,
+                 const double *amp) {
+  const size_t N = (size_t)nx * ny;
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (int s = 0; s < ns; ++s)
+    for (size_t site = 0; site < N; ++site) {
+      const uint32_t ctr[4] = {(uint32_t)site, (uint32_t)((uint64_t)site >> 32),
+                               (uint32_t)(1 + s), 0u};
+      uint32_t w[4];
+      lbo_philox4x32_10(ctr, key, w);
+      const double u = (double)w[0] * 0x1p-32;
+      const double rs = mean[s] + amp[s] * (2.0 * u - 1.0);
+      for (int i = 0; i < 9; ++i) f[(size_t)(s * 9 + i) * N + site] = w9(i) * rs;
+    }
+}
