@@ -60,6 +60,17 @@ SERVES = {
     "serve_f32": (1, 48, 50.0, tuple(range(64, 2049, 64)), (1e3, 1e5), 150e9, 64, 256),
     "serve_f16dev": (3, 48, 50.0, tuple(range(64, 2049, 64)), (1e3, 1e5), 150e9, 64, 256),
 }
+MIXES = {
+    # name: (nx, ny, storage): three species on a periodic lattice -- the A/B
+    # emulsion couplings (rho0 = 0.7, G^a = -9, G^r = 8.1, G_AB = 0.405) and a
+    # dilute third species C without self couplings, coupled to both by
+    # G_AC = G_BC = 0.2; rho = (1, 1, 0.1) +- (0.05, 0.05, 0.01)
+    "mix3_4096_f32": (4096, 4096, 1),
+    "mix3_1024_f32": (1024, 1024, 1),
+}
+MIX3 = dict(ns=3, tau=[1.0, 1.0, 1.0], rho0=0.7, Ga=[-9.0, -9.0, 0.0], Gr=[8.1, 8.1, 0.0],
+            G=[[0.0, 0.405, 0.2], [0.405, 0.0, 0.2], [0.2, 0.2, 0.0]])
+MIX3_INIT = ([1.0, 1.0, 0.1], [0.05, 0.05, 0.01])
 STORAGE_NAME = {0: "f64", 1: "f32", 2: "bf16dev", 3: "f16dev"}
 ELEM = {0: 8, 1: 4, 2: 2, 3: 2}
 
@@ -498,6 +509,60 @@ def run_gpu(args):
     D.close()
 
 
+def run_mix(args):
+    """An N_s = 3 species mixture (Sec. II for s = 1..N_s): MLUPS (site updates
+    of all three species per second) as the median over repeated blocks of
+    graph-free steps, against the bytes of 27 populations read and written."""
+    import torch
+
+    from paper_0906_3611_gb300 import lb
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    D = Dist()
+    nx, ny, storage = MIXES[args.workload]
+    m = MIX3
+    p = lb.make_mix_params(m["ns"], m["tau"], m["rho0"], m["Ga"], m["Gr"], m["G"],
+                           storage=storage)
+    stream = torch.cuda.Stream()
+    mx = lb.Mixture(nx, ny, p, stream=stream)
+    mx.init_random(rank, *MIX3_INIT)
+    mass0 = mx.observables()["mass"]
+    clocks = NvmlClocks(local)
+    clocks.start()
+    mx.step(args.warmup)
+    mx.sync()
+    ms = timed_blocks(D, stream, lambda: mx.step(args.steps), args.reps, clocks, args.target_s)
+    clocks_d = clocks.stop()
+    med = statistics.median(ms)
+    mass1 = mx.observables()["mass"]
+    status = mx.status()
+    mx.close()
+    sites = nx * ny
+    value = whole_job_mlups(D.sum(sites * args.steps), med * 1e-3)
+    bps = 2 * 9 * m["ns"] * ELEM[storage]
+    peak, peak_kind = peaks()
+    achieved = bps * sites / (med * 1e-3 / args.steps) / 1e9
+    if rank == 0:
+        line = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": med / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": STORAGE_NAME[storage], "data": "synthetic",
+                "config": {"workload": args.workload, "nx": nx, "ny": ny, "species": m["ns"],
+                           "boundary": "periodic", "storage": STORAGE_NAME[storage],
+                           "couplings": "A/B emulsion set + dilute C, G_AC = G_BC = 0.2",
+                           "timing": f"median of {len(ms)} timed blocks of {args.steps} steps",
+                           "l2": f"inputs larger than L2 ({bps // 2 * sites / 1e9:.2f} GB per buffer)"},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": None, "bytes_per_site": bps,
+                             "peak_kind": peak_kind},
+                "mass_drift": float(max(abs(mass1 / mass0 - 1))),
+                "gpu_launches": args.steps * len(ms), "clocks": clocks_d,
+                "status": lb.lb_strerror(status), "impl": "gb300"}
+        print(json.dumps(line), flush=True)
+    D.close()
+
+
 def run_sweep(args):
     """C3 at the Couette workload's size: every storage and wall speed, MLUPS and
     the FP64 stresses (mean sigma_xy, both walls) averaged over the second half
@@ -825,7 +890,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="couette4096_f32",
                     choices=sorted(WORKLOADS) + sorted(BATCHES) + sorted(SHEARS) + sorted(SERVES)
-                    + ["couette4096_sweep"])
+                    + sorted(MIXES) + ["couette4096_sweep"])
     ap.add_argument("--requests", type=int, default=0)
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -843,6 +908,8 @@ def main():
         run_reference(args)
     elif args.workload == "couette4096_sweep":
         run_sweep(args)
+    elif args.workload in MIXES:
+        run_mix(args)
     elif args.workload in BATCHES:
         run_batch(args)
     elif args.workload in SHEARS:

@@ -358,6 +358,65 @@ LB_API int lb_batch_status(lb_batch *b);
 /* Free the batch and every replica's buffers. */
 LB_API void lb_batch_destroy(lb_batch *b);
 
+/* ---- Mixtures of N_s species ----
+ * Sec. II writes Eq. (be) and Eq. (FORCE) for species s = 1..N_s: every
+ * species has its own relaxation time tau_s and self couplings G^a_s (first
+ * belt, weights w_i) and G^r_s (both belts, weights p_i), and a symmetric
+ * matrix G_ss' (s' != s) couples the species through
+ *   F^X_s = -(1/rho0^2) rho_s(r) sum_{s' != s} G_ss' sum_{i in belt 1} w_i rho_s'(r + c_i) c_i;
+ * the common velocity u = sum_s j_s/tau_s / sum_s rho_s/tau_s and the shifted
+ * equilibrium of Eq. (be) are as for two species.  A mixture lattice holds
+ * plain populations (FP64 or FP32, no reference shift) in its own layout:
+ * element (s, i, y, x) at ((s*9 + i)*ny + y)*pitch + x, pitch = nx rounded up
+ * to a multiple of 32.  Periodic or Couette (walls as for two species). */
+#define LB_MAX_SPECIES 4
+typedef struct lb_mix lb_mix; /* opaque, library-owned */
+typedef struct {
+  int ns;                                  /* number of species, 2 .. LB_MAX_SPECIES */
+  double tau[LB_MAX_SPECIES];              /* tau_s > 1/2                             */
+  double rho0;                             /* psi scale of Eq. (PSI), > 0             */
+  double Ga[LB_MAX_SPECIES];               /* G^a_s                                   */
+  double Gr[LB_MAX_SPECIES];               /* G^r_s                                   */
+  double G[LB_MAX_SPECIES][LB_MAX_SPECIES];/* G_ss', symmetric; the diagonal is unused */
+  int boundary;                            /* LB_PERIODIC or LB_COUETTE               */
+  double U_wall;                           /* Couette wall speed (top +U, bottom -U)  */
+  int storage;                             /* LB_F64 or LB_F32                        */
+} lb_mix_params;
+
+/* Create an nx x ny mixture (nx, ny >= 5) whose population buffers the
+ * library allocates on the current device; work is enqueued on cuda_stream
+ * (NULL: the legacy default stream).  LB_EINVAL for bad sizes or parameters
+ * (ns out of range, tau_s <= 1/2, an asymmetric G, a non-finite value),
+ * LB_ENOMEM, LB_ECUDA. */
+LB_API int lb_mix_create(int nx, int ny, const lb_mix_params *p, void *cuda_stream, lb_mix **out);
+
+/* Seeded initial state at rest: species s of site r = y*nx + x draws one
+ * Philox4x32-10 block with counter (r, 1 + s) and key seed; u = word_0 * 2^-32,
+ * rho_s = mean[s] + amp[s] (2u - 1), f_is = w_i rho_s.  mean and amp hold ns
+ * host values each.  Asynchronous. */
+LB_API int lb_mix_init_random(lb_mix *m, uint64_t seed, const double *mean, const double *amp);
+
+/* Enqueue n steps of Eq. (be) for every species.  Asynchronous. */
+LB_API int lb_mix_step(lb_mix *m, int64_t n);
+
+/* FP64 reductions of the current state (synchronises): mass[ns] = sum over
+ * sites of rho_s (may be NULL), momentum[2] = sum_s sum_i f_is c_i (may be
+ * NULL). */
+LB_API int lb_mix_observables(lb_mix *m, double *mass, double *momentum);
+
+/* Copy the state out as FP64 f[s][i][y][x] (ns*9*ny*nx host doubles), or
+ * replace it (converted to the storage type, round-to-nearest); both
+ * synchronise. */
+LB_API int lb_mix_get_state(lb_mix *m, double *f);
+LB_API int lb_mix_set_state(lb_mix *m, const double *f);
+
+/* Read and clear the mixture's device status word, as lb_status. */
+LB_API int lb_mix_status(lb_mix *m);
+
+/* Wait for the mixture's enqueued work; free it and its buffers. */
+LB_API int lb_mix_sync(lb_mix *m);
+LB_API void lb_mix_destroy(lb_mix *m);
+
 /* Static text for an error code. */
 LB_API const char *lb_strerror(int code);
 

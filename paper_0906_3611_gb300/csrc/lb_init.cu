@@ -13,24 +13,6 @@ size_t elem_size(int storage) {
   return 0;
 }
 
-// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds; each round
-// multiplies words 0 and 2 by the two Philox multipliers, mixes the high
-// halves with words 1 and 3 and the round key, and the key is bumped by the
-// two Weyl constants between rounds.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    if (r > 0) {
-      k0 += 0x9E3779B9u;
-      k1 += 0xBB67AE85u;
-    }
-    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-  }
-  return c;
-}
-
 // Convert an FP64 deviation to the storage type with one rounding (RN-even).
 template <int STORAGE>
 __device__ __forceinline__ typename Store<STORAGE>::T from_double(double v);

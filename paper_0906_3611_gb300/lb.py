@@ -34,7 +34,11 @@ EXPORTED = ["lb_state_bytes", "lb_create", "lb_create_on", "lb_init_random", "lb
             "lb_batch_get_state", "lb_batch_set_state",
             "lb_batch_series_start", "lb_batch_series_read", "lb_batch_series_stop", "lb_batch_shear_diagnostics", "lb_batch_phi_snapshot",
             "lb_batch_phi_overlap", "lb_batch_autotune", "lb_batch_set_layout",
-            "lb_batch_status", "lb_batch_destroy"]
+            "lb_batch_status", "lb_batch_destroy",
+            "lb_mix_create", "lb_mix_init_random", "lb_mix_step", "lb_mix_observables",
+            "lb_mix_get_state", "lb_mix_set_state", "lb_mix_status", "lb_mix_sync",
+            "lb_mix_destroy"]
+LB_MAX_SPECIES = 4
 
 
 class lb_params(ctypes.Structure):
@@ -44,6 +48,13 @@ class lb_params(ctypes.Structure):
                 ("rho_ref", ctypes.c_double * 2), ("init_kind", ctypes.c_int),
                 ("init", ctypes.c_double * 6), ("g_kolmo", ctypes.c_double),
                 ("k_kolmo", ctypes.c_int)]
+
+
+class lb_mix_params(ctypes.Structure):
+    _fields_ = [("ns", ctypes.c_int), ("tau", ctypes.c_double * 4), ("rho0", ctypes.c_double),
+                ("Ga", ctypes.c_double * 4), ("Gr", ctypes.c_double * 4),
+                ("G", (ctypes.c_double * 4) * 4), ("boundary", ctypes.c_int),
+                ("U_wall", ctypes.c_double), ("storage", ctypes.c_int)]
 
 
 class LBError(RuntimeError):
@@ -113,6 +124,16 @@ def _load():
                                              ctypes.POINTER(ctypes.c_int)]),
         "lb_batch_status": (ctypes.c_int, [vp]),
         "lb_batch_destroy": (None, [vp]),
+        "lb_mix_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(lb_mix_params),
+                                         vp, hp]),
+        "lb_mix_init_random": (ctypes.c_int, [vp, ctypes.c_uint64, dp, dp]),
+        "lb_mix_step": (ctypes.c_int, [vp, ctypes.c_int64]),
+        "lb_mix_observables": (ctypes.c_int, [vp, dp, dp]),
+        "lb_mix_get_state": (ctypes.c_int, [vp, dp]),
+        "lb_mix_set_state": (ctypes.c_int, [vp, dp]),
+        "lb_mix_status": (ctypes.c_int, [vp]),
+        "lb_mix_sync": (ctypes.c_int, [vp]),
+        "lb_mix_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -606,3 +627,113 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ---- mixtures of N_s species ----
+
+def make_mix_params(ns: int, tau, rho0: float, Ga, Gr, G, boundary: int = LB_PERIODIC,
+                    U_wall: float = 0.0, storage: int = LB_F32) -> lb_mix_params:
+    """lb_mix_params for ns species: tau, Ga, Gr of length ns, G an ns x ns
+    symmetric matrix (its diagonal is not used)."""
+    p = lb_mix_params()
+    p.ns = int(ns)
+    for s_ in range(ns):
+        p.tau[s_] = float(tau[s_])
+        p.Ga[s_] = float(Ga[s_])
+        p.Gr[s_] = float(Gr[s_])
+        for t in range(ns):
+            p.G[s_][t] = float(np.asarray(G)[s_][t])
+    p.rho0 = float(rho0)
+    p.boundary = int(boundary)
+    p.U_wall = float(U_wall)
+    p.storage = int(storage)
+    return p
+
+
+def lb_mix_create(nx: int, ny: int, params: lb_mix_params, stream: int | None = None) -> int:
+    m = ctypes.c_void_p()
+    _check(_lib.lb_mix_create(nx, ny, ctypes.byref(params), ctypes.c_void_p(stream or 0),
+                              ctypes.byref(m)), "lb_mix_create")
+    return m.value
+
+
+def lb_mix_init_random(m: int, seed: int, mean, amp) -> None:
+    mean = np.ascontiguousarray(mean, dtype=np.float64)
+    amp = np.ascontiguousarray(amp, dtype=np.float64)
+    _check(_lib.lb_mix_init_random(m, ctypes.c_uint64(seed), _dp(mean), _dp(amp)),
+           "lb_mix_init_random")
+
+
+def lb_mix_step(m: int, n: int) -> None:
+    _check(_lib.lb_mix_step(m, n), "lb_mix_step")
+
+
+def lb_mix_observables(m: int, ns: int) -> tuple[np.ndarray, np.ndarray]:
+    mass = np.zeros(ns)
+    mom = np.zeros(2)
+    _check(_lib.lb_mix_observables(m, _dp(mass), _dp(mom)), "lb_mix_observables")
+    return mass, mom
+
+
+def lb_mix_get_state(m: int, f: np.ndarray) -> None:
+    _check(_lib.lb_mix_get_state(m, _dp(f)), "lb_mix_get_state")
+
+
+def lb_mix_set_state(m: int, f: np.ndarray) -> None:
+    _check(_lib.lb_mix_set_state(m, _dp(f)), "lb_mix_set_state")
+
+
+def lb_mix_status(m: int) -> int:
+    return int(_lib.lb_mix_status(m))
+
+
+def lb_mix_sync(m: int) -> None:
+    _check(_lib.lb_mix_sync(m), "lb_mix_sync")
+
+
+def lb_mix_destroy(m: int) -> None:
+    _lib.lb_mix_destroy(m)
+
+
+class Mixture:
+    """An nx x ny lattice of ns species on the current CUDA device (library-owned
+    buffers); ``stream`` is a torch.cuda.Stream (default: a new one)."""
+
+    def __init__(self, nx: int, ny: int, params: lb_mix_params, stream=None):
+        import torch
+
+        self.nx, self.ny, self.ns, self.params = nx, ny, params.ns, params
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.h = lb_mix_create(nx, ny, params, self.stream.cuda_stream)
+
+    def init_random(self, seed: int, mean, amp):
+        lb_mix_init_random(self.h, seed, mean, amp)
+        return self
+
+    def step(self, n: int = 1):
+        lb_mix_step(self.h, n)
+        return self
+
+    def observables(self) -> dict:
+        mass, mom = lb_mix_observables(self.h, self.ns)
+        return {"mass": mass, "momentum": mom}
+
+    def get_state(self) -> np.ndarray:
+        f = np.empty((self.ns, 9, self.ny, self.nx))
+        lb_mix_get_state(self.h, f)
+        return f
+
+    def set_state(self, f: np.ndarray):
+        lb_mix_set_state(self.h, np.ascontiguousarray(f, dtype=np.float64))
+        return self
+
+    def status(self) -> int:
+        return lb_mix_status(self.h)
+
+    def sync(self):
+        lb_mix_sync(self.h)
+
+    def close(self):
+        if self.h:
+            lb_mix_destroy(self.h)
+            self.h = None

@@ -92,3 +92,38 @@ def test_invalid_arguments_of_the_newer_calls_without_gpu(lib):
     h = ctypes.c_void_p()
     for bad in (lb.make_params(g_kolmo=1e-3, k_kolmo=0), lb.make_params(g_kolmo=float("nan"))):
         assert lib.lb_create(64, 64, ctypes.byref(bad), None, ctypes.byref(h)) == E
+
+
+def test_mixture_parameters_are_validated_without_gpu(lib):
+    """lb_mix_create refuses bad species counts, tau_s <= 1/2, an asymmetric
+    cross-coupling matrix, 16-bit storage and non-finite values before any
+    device work; NULL handles are refused by every lb_mix call."""
+    from paper_0906_3611_gb300 import lb
+    E = lb.LB_EINVAL
+    G = [[0, 0.4, 0.2], [0.4, 0, 0.3], [0.2, 0.3, 0]]
+    ok = dict(ns=3, tau=[1, 1, 1], rho0=0.7, Ga=[-9, -9, 0], Gr=[8.1, 8.1, 0], G=G)
+    h = ctypes.c_void_p()
+
+    def create(**kw):
+        args = dict(ok, **kw)
+        return lib.lb_mix_create(64, 64, ctypes.byref(lb.make_mix_params(**args)), None,
+                                 ctypes.byref(h))
+
+    bad_G = [[0, 0.4, 0.2], [0.41, 0, 0.3], [0.2, 0.3, 0]]
+    assert create(G=bad_G) == E
+    assert create(tau=[1, 0.5, 1]) == E
+    assert create(storage=lb.LB_F16_DEV) == E
+    assert create(rho0=float("nan")) == E
+    assert create(boundary=2) == E
+    p5 = lb.make_mix_params(**ok)
+    p5.ns = 5
+    assert lib.lb_mix_create(64, 64, ctypes.byref(p5), None, ctypes.byref(h)) == E
+    p1 = lb.make_mix_params(**ok)
+    p1.ns = 1
+    assert lib.lb_mix_create(64, 64, ctypes.byref(p1), None, ctypes.byref(h)) == E
+    assert lib.lb_mix_create(4, 64, ctypes.byref(lb.make_mix_params(**ok)), None,
+                             ctypes.byref(h)) == E
+    assert lib.lb_mix_step(None, 1) == E
+    assert lib.lb_mix_observables(None, None, None) == E
+    assert lib.lb_mix_status(None) == E
+    assert lib.lb_mix_sync(None) == E
