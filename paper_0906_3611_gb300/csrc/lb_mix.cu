@@ -41,27 +41,22 @@ struct MixPhys {
   C rho0, inv_rho0;
   C Wpsi[LB_MAX_SPECIES][5];            // G^a_s w_k + G^r_s p_k per |c|^2 group (1, 2, 4, 5, 8)
   C gX[LB_MAX_SPECIES][LB_MAX_SPECIES];  // G_ss' / rho0^2 (zero on the diagonal)
+  C Wd[LB_MAX_SPECIES][12][2];           // Wpsi of pair k times its (c_x, c_y) (see kMixPairs)
   C Uwall;
 };
+
+// One direction (dx, dy) of each of the twelve opposite pairs of the 24-speed
+// forcing lattice (the other direction is (-dx, -dy)).
+__host__ __device__ constexpr int pair_dx(int k) { return k < 2 ? k + 1 : (k - 2) % 5 - 2; }
+__host__ __device__ constexpr int pair_dy(int k) { return k < 2 ? 0 : (k < 7 ? 1 : 2); }
 
 __host__ __device__ __forceinline__ size_t midx(const MixGeom& g, int s, int i, int y, int x) {
   return (size_t)(s * 9 + i) * (size_t)g.plane + (size_t)y * (size_t)g.pitch + (size_t)x;
 }
 
-template <typename T>
-struct MixType;
-template <>
-struct MixType<double> {
-  static __device__ __forceinline__ double st(double v) { return v; }
-};
-template <>
-struct MixType<float> {
-  static __device__ __forceinline__ float st(float v) { return v; }
-};
-
 // One step of every species (src -> dst) on a 32 x 8 tile per CTA.
 template <int NS, typename C>
-__global__ void __launch_bounds__(MTH)
+__global__ void __launch_bounds__(MTH, sizeof(C) == 4 ? 3 : 1)
     k_mix(const C* __restrict__ src, C* __restrict__ dst, MixGeom g, MixPhys<C> ph,
           Status* status) {
   __shared__ C s_rho[NS][MEY][MEX];
@@ -105,40 +100,37 @@ __global__ void __launch_bounds__(MTH)
   }
   const C ux = div_c<C>(nux, den), uy = div_c<C>(nuy, den);
 
-  // belt-1 density sums of every species (shared by the pair terms)
+  // belt-1 density sums of every species (shared by the pair terms): the
+  // four opposite pairs of belt 1 enter as differences
   C Xx[NS], Xy[NS];
 #pragma unroll
   for (int t = 0; t < NS; ++t) {
-    C ax = C(0), ay = C(0);
-#pragma unroll
-    for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-      for (int dx = -1; dx <= 1; ++dx) {
-        if (dx == 0 && dy == 0) continue;
-        const C w = (dx != 0 && dy != 0) ? wq<C>(5) : wq<C>(1);
-        const C ro = s_rho[t][ty + 2 + dy][tx + 2 + dx];
-        ax += w * ro * C(dx);
-        ay += w * ro * C(dy);
-      }
-    Xx[t] = ax;
-    Xy[t] = ay;
+    const C(*r)[MEX] = s_rho[t];
+    const int a = ty + 2, b = tx + 2;
+    const C e = r[a][b + 1] - r[a][b - 1];          // (+-1, 0)
+    const C n = r[a + 1][b] - r[a - 1][b];          // (0, +-1)
+    const C d1 = r[a + 1][b + 1] - r[a - 1][b - 1];  // (1, 1) and (-1, -1)
+    const C d2 = r[a + 1][b - 1] - r[a - 1][b + 1];  // (-1, 1) and (1, -1)
+    Xx[t] = wq<C>(1) * e + wq<C>(5) * (d1 - d2);
+    Xy[t] = wq<C>(1) * n + wq<C>(5) * (d1 + d2);
   }
 
   int bad = 0;
   const bool couette = g.boundary == LB_COUETTE;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
+    // psi stencil over both belts, the twelve opposite pairs as differences:
+    // sum_c W(c) psi(r + c) c = sum over pairs W(c) c [psi(r + c) - psi(r - c)]
     C sx = C(0), sy = C(0);
+    const C(*q)[MEX] = s_psi[s];
+    const int a = ty + 2, b = tx + 2;
 #pragma unroll
-    for (int dy = -2; dy <= 2; ++dy)
-#pragma unroll
-      for (int dx = -2; dx <= 2; ++dx) {
-        if (dx == 0 && dy == 0) continue;
-        const C ps = s_psi[s][ty + 2 + dy][tx + 2 + dx];
-        const C wk = ph.Wpsi[s][group_of(dx, dy)];
-        sx += wk * ps * C(dx);
-        sy += wk * ps * C(dy);
-      }
+    for (int k = 0; k < 12; ++k) {
+      const int dx = pair_dx(k), dy = pair_dy(k);
+      const C diff = q[a + dy][b + dx] - q[a - dy][b - dx];
+      if (dx != 0) sx += ph.Wd[s][k][0] * diff;
+      if (dy != 0) sy += ph.Wd[s][k][1] * diff;
+    }
     C fxx = C(0), fxy = C(0);
 #pragma unroll
     for (int t = 0; t < NS; ++t) {
@@ -273,6 +265,12 @@ MixPhys<C> make_mix_phys(const lb_mix_params& p) {
     m.omega[s] = (C)(1.0 / p.tau[s]);
     m.tau[s] = (C)p.tau[s];
     for (int k = 0; k < 5; ++k) m.Wpsi[s][k] = (C)(p.Ga[s] * table_w(k) + p.Gr[s] * table_p(k));
+    for (int k = 0; k < 12; ++k) {
+      const int dx = pair_dx(k), dy = pair_dy(k);
+      const double wk = p.Ga[s] * table_w(group_of(dx, dy)) + p.Gr[s] * table_p(group_of(dx, dy));
+      m.Wd[s][k][0] = (C)(wk * dx);
+      m.Wd[s][k][1] = (C)(wk * dy);
+    }
     for (int t = 0; t < p.ns; ++t) m.gX[s][t] = (C)(t == s ? 0.0 : p.G[s][t] / r2);
   }
   m.rho0 = (C)p.rho0;
