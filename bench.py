@@ -448,7 +448,7 @@ def run_gpu(args):
     prof = os.path.join(ROOT, "profiles", "traffic.txt")
     if os.path.exists(prof):
         from paper_0906_3611_gb300 import build as _b
-        sha = _b.kernel_sha()
+        sha = _b.rows_kernel_sha()
         for line in open(prof):
             if line.startswith(f"{args.workload} ") and "kernel_sha=" in line:
                 parts = dict(kv.split("=", 1) for kv in line.split()[1:] if "=" in kv)

@@ -45,6 +45,22 @@ def kernel_sha() -> str:
     return h.hexdigest()[:12]
 
 
+# the sources the row-streaming step kernels are compiled from (a profile of
+# k_rows / k_rows_batch stays valid while these are unchanged)
+ROWS_SOURCES = ("lb_common.cuh", "lb_pair.cuh", "lb_site.cuh", "lb_kernels.h", "lb_rows.h",
+                "lb_rows.cuh", "lb_rows.cu", "lb_rows_batch.cu")
+
+
+def rows_kernel_sha() -> str:
+    """Short hash of the row-streaming kernels' sources."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in ROWS_SOURCES:
+        h.update(name.encode())
+        h.update(open(os.path.join(CSRC, name), "rb").read())
+    return h.hexdigest()[:12]
+
+
 def _stale() -> bool:
     if not os.path.exists(LIB):
         return True

@@ -100,7 +100,7 @@ constexpr size_t rows_smem_bytes() {
   using T2 = typename PairStore<STORAGE>::T2;
   using P = typename PairOf<typename Store<STORAGE>::C>::P;
   return (size_t)RowsCfg<STORAGE>::NSLOT * 9 * stage_width<STORAGE>() * sizeof(T2) +
-         (size_t)RowsCfg<STORAGE>::NCW * 2 * WEXT * sizeof(P) + 2 * 8 * RowsCfg<STORAGE>::NSLOT;
+         (size_t)RowsCfg<STORAGE>::NCW * 2 * WEXT * sizeof(P) + (2 * RowsCfg<STORAGE>::NSLOT + 1) * 8;
 }
 
 // ---- programmatic dependent launch ----
@@ -169,33 +169,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return done != 0;
 }
-// Non-blocking test of a phase (try_wait may suspend the thread for a while
-// before it reports an incomplete phase; test_wait answers at once).
-__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t done;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(done)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-
 // Bounded wait of a whole converged warp: every lane polls, and the lanes
 // decide together (warp votes) whether the phase completed or the bound ran
-// out, so the warp leaves the wait converged whatever the outcome.  With a
-// bound shorter than the default (the test hook) the polls do not suspend, so
-// that the bound is what ends the wait.
+// out, so the warp leaves the wait converged whatever the outcome.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit) {
-  if (limit < kWaitLimitDefault) {
-    const long long t0 = clock64();
-    while (true) {
-      if (__all_sync(0xffffffffu, mbar_test_wait(bar, parity))) return true;
-      if (__any_sync(0xffffffffu, clock64() - t0 > limit)) return false;
-    }
-  }
   if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
   const long long t0 = clock64();
   while (true) {
@@ -268,6 +245,7 @@ struct RowsSmem {
   P* rowbuf;      // per compute warp: WEXT rho pairs, WEXT psi pairs
   uint64_t* full;   // NSLOT mbarriers: bytes of the staged row landed
   uint64_t* empty;  // NSLOT mbarriers: every compute warp released the slot
+  uint64_t* never;  // an mbarrier nothing arrives on (the timeout test hook waits on it)
   __device__ __forceinline__ explicit RowsSmem(unsigned char* smem) {
     stage = reinterpret_cast<T2*>(smem);
     size_t off = (size_t)NSLOT * SLOT * sizeof(T2);
@@ -275,12 +253,14 @@ struct RowsSmem {
     off += (size_t)NCW * 2 * WEXT * sizeof(P);
     full = reinterpret_cast<uint64_t*>(smem + off);
     empty = full + NSLOT;
+    never = empty + NSLOT;
   }
   __device__ __forceinline__ void init() {  // thread 0, before the first __syncthreads
     for (int k = 0; k < NSLOT; ++k) {
       mbar_init(&full[k], 1);
       mbar_init(&empty[k], NCW);
     }
+    mbar_init(never, 1);
     mbar_fence_init();
   }
 };
@@ -409,20 +389,6 @@ struct RowsLoop {
       issue_row<STORAGE>(src, sm.stage + s * SLOT, &sm.full[s], g, x0, ylo - 2 + j, lane);
     }
     issued = j;
-  }
-
-  // After an abort (called by one thread of the staging warp, once every warp
-  // of the CTA has left the range): wait, bounded, for the copies still in
-  // flight, so that none is writing into this CTA's shared memory when it
-  // moves on or exits.  Only the last NSLOT issued rows can be outstanding: a
-  // slot is refilled only after its previous row was consumed.
-  __device__ __forceinline__ void drain() const {
-    for (int k = (issued > NSLOT ? issued - NSLOT : 0); k < issued; ++k) {
-      const long long t0 = clock64();
-      while (!mbar_try_wait(&sm.full[slot_of(k)], round_of(k) & 1)) {
-        if (clock64() - t0 > kWaitLimitDefault) break;
-      }
-    }
   }
 
   // rho, drho and psi pairs of staged column c (0 .. SW-1) of a staged row
@@ -577,8 +543,13 @@ struct RowsLoop {
       atomicAdd(&sr.buf[sr.step % sr.cap], v);
   }
 
+  // Wait for staged row j.  Under the test hook (a bound shorter than the
+  // default) the warp waits on a barrier that nothing completes instead, so
+  // that the bound, not the copy, ends the wait.
   __device__ __forceinline__ bool wait_row(int j) {
-    if (!mbar_wait_bounded(&sm.full[slot_of(j)], round_of(j) & 1, wait_limit)) {
+    const bool hook = wait_limit < kWaitLimitDefault;
+    if (!mbar_wait_bounded(hook ? sm.never : &sm.full[slot_of(j)], hook ? 0u : round_of(j) & 1,
+                           wait_limit)) {
       if (lane == 0) {
         atomicExch(&status->timeout, 1u);
         *s_abort = 1;
@@ -841,6 +812,23 @@ struct RowsLoop {
 
 };
 
+// After an abort (one thread of the staging warp, once every warp of the CTA
+// has left the range): wait, bounded, for the copies still in flight, so that
+// none is writing into this CTA's shared memory when it moves on or exits.
+// Rows ring0 .. ring0 + issued - 1 of the slot ring were issued; only the last
+// NSLOT can be outstanding (a slot is refilled only after its row was consumed).
+template <int STORAGE>
+__device__ __noinline__ void drain_copies(const RowsSmem<STORAGE>& sm, int ring0, int issued) {
+  constexpr int NSLOT = RowsCfg<STORAGE>::NSLOT;
+  for (int k = (issued > NSLOT ? issued - NSLOT : 0); k < issued; ++k) {
+    const int j = ring0 + k;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(&sm.full[j % NSLOT], (uint32_t)(j / NSLOT) & 1)) {
+      if (clock64() - t0 > kWaitLimitDefault) break;
+    }
+  }
+}
+
 // One CTA, one work range: columns x0 .. x1-1 (at most RX), output rows
 // ylo .. yhi-1 of the lattice (src -> dst).  `ring` is the position of the
 // next staged row in the CTA's slot ring (identical in every thread); on
@@ -855,18 +843,25 @@ __device__ __forceinline__ void rows_range(
     const typename Store<STORAGE>::C* body, int x0, int x1, int ylo, int yhi,
     const RowsSmem<STORAGE>& sm, int& ring, int* s_abort, Status* status, int& bad,
     const Series& sr, long long wait_limit) {
-  RowsLoop<STORAGE, BODY, LAG> L(src, dst, g, ph, Uwall, body, x0, x1, ylo, yhi, sm, ring,
-                                 s_abort, status, sr, wait_limit);
-  if (L.warp == RowsCfg<STORAGE>::NCW)
-    L.produce();
-  else
-    L.consume();
+  const int ring0 = ring;
+  int issued = 0;
+  {
+    RowsLoop<STORAGE, BODY, LAG> L(src, dst, g, ph, Uwall, body, x0, x1, ylo, yhi, sm, ring,
+                                   s_abort, status, sr, wait_limit);
+    if (L.warp == RowsCfg<STORAGE>::NCW) {
+      L.produce();
+      issued = L.issued;
+    } else {
+      L.consume();
+    }
+    bad += L.bad;
+  }
+  ring += (yhi - ylo) + 4;
   // every warp has left the range: after an abort the staging warp waits for
   // the copies it issued that may still be landing
   __syncthreads();
-  if (*(volatile int*)s_abort && L.warp == RowsCfg<STORAGE>::NCW && L.lane == 0) L.drain();
-  bad += L.bad;
-  ring += L.nstage;
+  if (*(volatile int*)s_abort && threadIdx.x == 32 * RowsCfg<STORAGE>::NCW)
+    drain_copies<STORAGE>(sm, ring0, issued);
 }
 
 // Resident CTAs per SM of a kernel variant at the row kernels' shared memory.
