@@ -1,14 +1,24 @@
 """Reduced-precision storage: FP32 arithmetic on populations stored as BF16 or
 FP16 deviations d_i = f_i - w_i rho_ref,s, against the FP64 oracle.
 
-Stated bounds (measured on GB300, then given a ~3x margin):
-* one step from a state near rho_ref: max relative population error
-  <= 1e-3 (BF16, 8-bit significand) and <= 1e-4 (FP16, 11-bit), both step
-  kernels, both boundary kinds;
-* per-species mass drift of the 512 x 512 Bernoulli droplet emulsion after
-  1000 steps (rho_ref = the species means): FP32 <= 1e-6, FP16 <= 2e-4,
-  BF16 <= 5e-4 (measured 1e-8, 2e-5, 5e-5: ~10x margin, the 16-bit drift
-  being a random walk).  The collision conserves rho_s, so the kernels give
+* One step from a state near rho_ref, both step kernels, both boundary kinds:
+  every population within a bound derived from the storage format, with no
+  fitted factor.  The oracle steps the stored (rounded) state, so the GPU's
+  error is (1) the FP32 arithmetic, held to the FP32 bar 1e-5 w_i rho_s;
+  (2) the round-to-nearest of each stored moving deviation, at most
+  u |d*_i| (u = 2^-11 FP16, 2^-8 BF16) plus half the smallest subnormal
+  spacing; (3) for the rest population, which takes what the eight stored
+  moving populations leave of the site's density deviation, the sum of those
+  eight roundings plus its own stochastic rounding (under one unit in the
+  last place, 2u |d*_0|).
+* Per-species mass drift of the 512 x 512 Bernoulli droplet emulsion after
+  1000 steps (rho_ref = the species means): FP32 <= 1e-6 (stated; measured
+  1e-8); the 16-bit drift is a random walk of one stochastic rounding per site
+  and step, of at most one unit in the last place of |d_0| <= 4/9 |rho -
+  rho_ref| <= 0.35 (variance <= ulp^2/6), so its relative standard deviation is
+  ulp sqrt(T / (6 N)) / <rho_s> and the bound four of those (FP16 ulp 2^-12:
+  5.7e-5, BF16 ulp 2^-9: 4.6e-4 with <rho_B> = 0.43; measured 2e-5, 5e-5).
+  The collision conserves rho_s, so the kernels give
   the rest population what the eight stored moving populations leave of the
   site's density, and the 16-bit storages round that one population
   stochastically: the only mass error left is the zero-mean rounding of the
@@ -41,26 +51,56 @@ def _rel(a, b):
     return float(np.max(np.abs(a - b) / np.abs(b)))
 
 
+UNIT = {"f16": 2.0 ** -11, "bf16": 2.0 ** -8}      # unit roundoff of the storage
+SUBNORMAL = {"f16": 2.0 ** -25, "bf16": 2.0 ** -134}  # half the smallest spacing
+
+
+def _storage_bound(ref, rho_ref, storage):
+    """Elementwise bound of one 16-bit step against the oracle's step of the
+    same stored state (see the module docstring)."""
+    u, a = UNIT[storage], SUBNORMAL[storage]
+    rr = np.asarray(rho_ref, dtype=np.float64)[:, None, None, None]
+    dev = np.abs(ref - W9[None, :, None, None] * rr)  # |d*_i| as the storage holds it
+    rho = np.abs(ref.sum(axis=1))[:, None]
+    bound = u * dev + a + 1e-5 * W9[None, :, None, None] * rho
+    moving = (u * dev[:, 1:] + a).sum(axis=1)
+    bound[:, 0] = 2 * u * dev[:, 0] + 2 * a + moving + 1e-5 * W9[0] * rho[:, 0]
+    return bound
+
+
 @pytest.mark.parametrize("kernel", ["rows", "tile"])
 @pytest.mark.parametrize("boundary,U", [(0, 0.0), (1, 0.03)])
-@pytest.mark.parametrize("storage,tol", [("bf16", 1e-3), ("f16", 1e-4)])
-def test_one_step_near_reference_state(lb, monkeypatch, kernel, boundary, U, storage, tol):
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_one_step_near_reference_state(lb, monkeypatch, kernel, boundary, U, storage):
     st = {"bf16": lb.LB_BF16_DEV, "f16": lb.LB_F16_DEV}[storage]
     monkeypatch.setenv("LB_STEP_KERNEL", kernel)
     nx, ny = 264, 40
-    f = inputs.populations(nx, ny, seed=3, base=W9, rel_amp=0.05, species_scale=(0.9, 1.1))
-    p = lb.make_params(**CFG, boundary=boundary, U_wall=U, storage=st, rho_ref=(0.9, 1.1))
+    rho_ref = (0.9, 1.1)
+    f = inputs.populations(nx, ny, seed=3, base=W9, rel_amp=0.05, species_scale=rho_ref)
+    p = lb.make_params(**CFG, boundary=boundary, U_wall=U, storage=st, rho_ref=rho_ref)
     lat = lb.Lattice(nx, ny, p)
     f0 = lat.set_state(f).get_state()  # the stored (rounded) state
     g = lat.step(1).get_state()
     assert lat.status() == lb.LB_OK
     lat.close()
     ref, _ = oracle.step(f0, dict(CFG, boundary=boundary, U_wall=U), 1)
-    assert _rel(g, ref) <= tol
+    err = np.abs(g - ref)
+    bound = _storage_bound(ref, rho_ref, storage)
+    worst = float(np.max(err / bound))
+    print(f"{kernel} {storage} bd={boundary}: worst error / bound {worst:.2f}", end=" ")
+    assert worst <= 1.0
+    # the rounding is real: the error exceeds what FP32 arithmetic alone leaves
+    assert float(np.max(err / (1e-5 * W9[None, :, None, None] * np.abs(ref.sum(axis=1))[:, None]))) > 1.0
 
 
-@pytest.mark.parametrize("storage,bound", [("f32", 1e-6), ("f16", 2e-4), ("bf16", 5e-4)])
-def test_mass_drift_of_the_droplet_emulsion(lb, storage, bound):
+def _walk_bound(storage, steps=1000, sites=512 * 512, rho_mean=0.43):
+    ulp = {"f16": 2.0 ** -12, "bf16": 2.0 ** -9}[storage]
+    return 4.0 * ulp * np.sqrt(steps / (6.0 * sites)) / rho_mean
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_mass_drift_of_the_droplet_emulsion(lb, storage):
+    bound = 1e-6 if storage == "f32" else _walk_bound(storage)
     st = {"f32": lb.LB_F32, "f16": lb.LB_F16_DEV, "bf16": lb.LB_BF16_DEV}[storage]
     p = lb.make_params(**CFG, storage=st, rho_ref=(0.88, 0.44), init_kind=lb.LB_INIT_BERNOULLI,
                        init=(0.7, 1.2, 0.1, 0.02))
