@@ -762,11 +762,14 @@ struct RowsLoop {
   __device__ __forceinline__ void push(int o, P (&d)[9], P rho, P drho) {
     // 16-bit storages round the rest population stochastically; the bits are
     // hashed from the site and its relaxed populations (deterministic runs),
-    // one hash per site pair
+    // one short hash per site pair: a multiply by an odd constant spreads the
+    // key into the high bits, the xor-shift folds them into the low ones
     uint32_t rbits = 0;
-    if (sizeof(T2) == 4)
-      rbits = mix32(__float_as_uint((float)d[1].x) ^ (__float_as_uint((float)d[6].y) << 7) ^
-                    ((uint32_t)x * 0x9E3779B1u) ^ ((uint32_t)o * 0x85EBCA77u));
+    if (sizeof(T2) == 4) {
+      rbits = (__float_as_uint((float)d[1].x) ^ (__float_as_uint((float)d[6].y) << 7) ^
+               ((uint32_t)x * 0x85EBCA77u) ^ ((uint32_t)o * 0xC2B2AE3Du)) * 0x9E3779B1u;
+      rbits ^= rbits >> 16;
+    }
     const bool wall = (g.boundary == LB_COUETTE) && (o == 0 || o == g.ny - 1);
     if (!wall) {
       // row and plane offsets (32-bit: rows_geometry_ok bounds 9 planes
