@@ -227,9 +227,10 @@ LB_API int64_t lb_time(const lb_handle *h);
  * skipped there), or LB_ETIMEOUT (a bounded wait of the row-streaming kernel
  * for a staged row gave up -- about a second by default -- and the step was
  * abandoned: the state is then undefined until lb_set_state or
- * lb_init_random).  Test hook: the environment variable LB_TEST_WAIT_CYCLES,
- * read by lb_create / lb_batch_create, shortens that bound to the given
- * number of SM cycles, so that the timeout path can be exercised. */
+ * lb_init_random).  Test hook: the environment variable LB_TEST_STALL_STAGING
+ * set to a nonzero integer, read by lb_create / lb_batch_create, makes the
+ * row kernel issue no copy of a staged row, so that its waits run out and the
+ * timeout path can be exercised (each step then takes about a second). */
 LB_API int lb_status(lb_handle *h);
 
 /* Wait for all work enqueued by this handle. */

@@ -38,7 +38,7 @@ struct lb_handle {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int graph_steps = 0;
   int use_rows = 0;       // 1 if the row-streaming kernel serves this lattice
-  long long wait_limit = kWaitLimitDefault;  // bound of the row kernel's waits (cycles)
+  int stall = 0;  // the row kernel's timeout test hook (stall_from_env)
   Series sr{nullptr, nullptr, nullptr, 0, 0, 0u};  // shear-response record (off by default)
 };
 
@@ -124,7 +124,7 @@ static int create_common(int nx, int ny, const lb_params* p, void* stream, void*
   // step kernel: the row-streaming kernel where it applies, else the tile
   // kernel; LB_STEP_KERNEL=tile|rows forces one (for testing both paths)
   // (by default the row kernel serves lattices at least 128 columns wide)
-  h->wait_limit = wait_limit_from_env(kWaitLimitDefault);
+  h->stall = stall_from_env();
   const char* kern = getenv("LB_STEP_KERNEL");
   const bool rows_ok = rows_supported(h->g, p->storage);
   if (kern && strcmp(kern, "tile") == 0)
@@ -196,7 +196,7 @@ static cudaError_t step_once(lb_handle* h, int from, cudaStream_t st) {
   void* dst = h->buf[1 - from];
   if (h->use_rows)
     return launch_step_rows(h->p.storage, src, dst, h->g, h->ph, h->d_body, h->d_status, h->sr,
-                            h->wait_limit, st);
+                            h->stall, st);
   return launch_step_tile(h->p.storage, src, dst, h->g, h->ph, h->d_status, h->sr, st);
 }
 

@@ -77,7 +77,7 @@ struct lb_batch {
                                       ? sizeof(PhysTable<double>)
                                       : sizeof(PhysTable<float>)] = {};
   int nphys = 0;
-  long long wait_limit = kWaitLimitDefault;  // bound of the row kernel's waits (cycles)
+  int stall = 0;  // the row kernel's timeout test hook (stall_from_env)
   bool body = false;  // some replica has a Kolmogorov body-force table
   bool rec = false;   // some replica keeps a shear-response record
   cudaStream_t cap_stream = nullptr;
@@ -399,7 +399,7 @@ extern "C" int lb_batch_create(int capacity, int storage, void* cuda_stream, lb_
     return LB_ECUDA;
   }
   b->grid = rows_batch_grid(storage);
-  b->wait_limit = wait_limit_from_env(kWaitLimitDefault);
+  b->stall = stall_from_env();
   if (cudaMalloc(&b->d_reps, (size_t)capacity * rep_bytes(storage)) != cudaSuccess ||
       cudaMalloc(&b->d_offsets, (size_t)(b->grid + 1) * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&b->d_status, sizeof(Status)) != cudaSuccess ||
@@ -516,7 +516,7 @@ extern "C" int lb_batch_set_steps(lb_batch* b, int slot, int64_t steps) {
 
 static cudaError_t batch_launch(lb_batch* b, cudaStream_t st) {
   return launch_step_rows_batch(b->storage, b->d_reps, b->d_items, b->d_offsets, b->grid,
-                                b->table, b->nphys, b->body, b->rec, b->d_status, b->wait_limit,
+                                b->table, b->nphys, b->body, b->rec, b->d_status, b->stall,
                                 st);
 }
 

@@ -29,17 +29,17 @@ struct PhysD {
   int dev;  // 1 for the deviation storages (every storage but FP64)
 };
 
-// Bound (SM cycles) of the row kernels' waits for a staged row: the default,
-// or LB_TEST_WAIT_CYCLES from the environment (read when a handle or batch is
-// created; a test hook that shortens the bound so that a wait gives up and
-// the timeout path runs -- the step then reports LB_ETIMEOUT).
-inline long long wait_limit_from_env(long long dflt) {
-  const char* v = getenv("LB_TEST_WAIT_CYCLES");
-  if (!v || !*v) return dflt;
+// The row kernels' timeout test hook: 1 when LB_TEST_STALL_STAGING is set to a
+// nonzero integer in the environment (read when a handle or batch is created),
+// else 0.  Under it the kernels' staging warps issue no copy, so the compute
+// warps' bounded waits run out (about a second) and the step reports
+// LB_ETIMEOUT.
+inline int stall_from_env() {
+  const char* v = getenv("LB_TEST_STALL_STAGING");
+  if (!v || !*v) return 0;
   char* end = nullptr;
-  const long long c = strtoll(v, &end, 10);
-  if (end == v || c < 0) return dflt;
-  return c < dflt ? c : dflt;
+  const long c = strtol(v, &end, 10);
+  return (end != v && c != 0) ? 1 : 0;
 }
 
 // Checks of the physics part of lb_params shared by every entry point that

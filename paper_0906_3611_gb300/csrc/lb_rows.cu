@@ -18,7 +18,7 @@ __global__ void __launch_bounds__(cta_threads<STORAGE>(), RowsCfg<STORAGE>::MINB
     k_rows(const typename PairStore<STORAGE>::T2* __restrict__ src,
            typename PairStore<STORAGE>::T2* __restrict__ dst, Geom g,
            Phys<typename Store<STORAGE>::C> ph, const typename Store<STORAGE>::C* body,
-           int nstrips, int kranges, Status* status, Series sr, long long wait_limit) {
+           int nstrips, int kranges, Status* status, Series sr, int stall) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_abort;
   RowsSmem<STORAGE> sm(smem);
@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(cta_threads<STORAGE>(), RowsCfg<STORAGE>::MINB
   int ring = 0, bad = 0;
   const Series none{};
   rows_range<STORAGE, (MODE > 0)>(src, dst, g, ph, ph.Uwall, body, x0, x1, ylo, yhi, sm, ring,
-                                  &s_abort, status, bad, MODE == 2 ? sr : none, wait_limit);
+                                  &s_abort, status, bad, MODE == 2 ? sr : none, stall);
   if (bad) atomicAdd(&status->bad_rho, (unsigned)bad);
 }
 
@@ -125,7 +125,7 @@ cudaError_t make_body_table(int storage, const PhysD& ph, int ny, void** out, cu
 template <int STORAGE>
 static cudaError_t rows_t(const void* src, void* dst, const Geom& g, const PhysD& pd,
                           const void* body_v, Status* status, const Series& sr_in,
-                          long long wait_limit, cudaStream_t st) {
+                          int stall, cudaStream_t st) {
   using C = typename Store<STORAGE>::C;
   const C* body = (const C*)body_v;
   using T2 = typename PairStore<STORAGE>::T2;
@@ -143,22 +143,22 @@ static cudaError_t rows_t(const void* src, void* dst, const Geom& g, const PhysD
   const bool dep = (long long)g.nx * g.ny < kDependentLaunchSites;
   if (sr.buf)
     return launch_step_kernel(dep, k_rows<STORAGE, 2>, nb, th, smem, st, s2, d2, g, ph, body,
-                              nstrips, k, status, sr, wait_limit);
+                              nstrips, k, status, sr, stall);
   if (body)
     return launch_step_kernel(dep, k_rows<STORAGE, 1>, nb, th, smem, st, s2, d2, g, ph, body,
-                              nstrips, k, status, sr, wait_limit);
+                              nstrips, k, status, sr, stall);
   return launch_step_kernel(dep, k_rows<STORAGE, 0>, nb, th, smem, st, s2, d2, g, ph, body,
-                            nstrips, k, status, sr, wait_limit);
+                            nstrips, k, status, sr, stall);
 }
 
 cudaError_t launch_step_rows(int storage, const void* src, void* dst, const Geom& g,
                              const PhysD& ph, const void* body, Status* status, const Series& sr,
-                             long long wait_limit, cudaStream_t st) {
+                             int stall, cudaStream_t st) {
   switch (storage) {
-    case LB_F64: return rows_t<LB_F64>(src, dst, g, ph, body, status, sr, wait_limit, st);
-    case LB_F32: return rows_t<LB_F32>(src, dst, g, ph, body, status, sr, wait_limit, st);
-    case LB_BF16_DEV: return rows_t<LB_BF16_DEV>(src, dst, g, ph, body, status, sr, wait_limit, st);
-    case LB_F16_DEV: return rows_t<LB_F16_DEV>(src, dst, g, ph, body, status, sr, wait_limit, st);
+    case LB_F64: return rows_t<LB_F64>(src, dst, g, ph, body, status, sr, stall, st);
+    case LB_F32: return rows_t<LB_F32>(src, dst, g, ph, body, status, sr, stall, st);
+    case LB_BF16_DEV: return rows_t<LB_BF16_DEV>(src, dst, g, ph, body, status, sr, stall, st);
+    case LB_F16_DEV: return rows_t<LB_F16_DEV>(src, dst, g, ph, body, status, sr, stall, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -35,8 +35,8 @@
 // Every mbarrier wait is bounded and taken by whole warps that decide together
 // (so a warp leaves a wait converged): on timeout the kernel sets the status
 // word, raises the CTA's abort flag, drains its own copies (bounded) and
-// leaves.  The bound of the compute warps' waits is a launch parameter (the
-// library's default ~2^31 cycles; a test hook shrinks it to exercise this path).
+// leaves.  A launch parameter (a test hook) makes the staging warp issue no
+// copy, so that the compute warps' waits run out and this path runs.
 #pragma once
 
 #include "lb_pair.cuh"
@@ -100,7 +100,7 @@ constexpr size_t rows_smem_bytes() {
   using T2 = typename PairStore<STORAGE>::T2;
   using P = typename PairOf<typename Store<STORAGE>::C>::P;
   return (size_t)RowsCfg<STORAGE>::NSLOT * 9 * stage_width<STORAGE>() * sizeof(T2) +
-         (size_t)RowsCfg<STORAGE>::NCW * 2 * WEXT * sizeof(P) + (2 * RowsCfg<STORAGE>::NSLOT + 1) * 8;
+         (size_t)RowsCfg<STORAGE>::NCW * 2 * WEXT * sizeof(P) + 2 * RowsCfg<STORAGE>::NSLOT * 8;
 }
 
 // ---- programmatic dependent launch ----
@@ -172,12 +172,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // Bounded wait of a whole converged warp: every lane polls, and the lanes
 // decide together (warp votes) whether the phase completed or the bound ran
 // out, so the warp leaves the wait converged whatever the outcome.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
   if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
   const long long t0 = clock64();
   while (true) {
     if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
-    if (__any_sync(0xffffffffu, clock64() - t0 > limit)) return false;
+    if (__any_sync(0xffffffffu, clock64() - t0 > kWaitLimitDefault)) return false;
   }
 }
 // The same with exponential sleep between polls, for a waiter that is far
@@ -245,7 +245,6 @@ struct RowsSmem {
   P* rowbuf;      // per compute warp: WEXT rho pairs, WEXT psi pairs
   uint64_t* full;   // NSLOT mbarriers: bytes of the staged row landed
   uint64_t* empty;  // NSLOT mbarriers: every compute warp released the slot
-  uint64_t* never;  // an mbarrier nothing arrives on (the timeout test hook waits on it)
   __device__ __forceinline__ explicit RowsSmem(unsigned char* smem) {
     stage = reinterpret_cast<T2*>(smem);
     size_t off = (size_t)NSLOT * SLOT * sizeof(T2);
@@ -253,14 +252,12 @@ struct RowsSmem {
     off += (size_t)NCW * 2 * WEXT * sizeof(P);
     full = reinterpret_cast<uint64_t*>(smem + off);
     empty = full + NSLOT;
-    never = empty + NSLOT;
   }
   __device__ __forceinline__ void init() {  // thread 0, before the first __syncthreads
     for (int k = 0; k < NSLOT; ++k) {
       mbar_init(&full[k], 1);
       mbar_init(&empty[k], NCW);
     }
-    mbar_init(never, 1);
     mbar_fence_init();
   }
 };
@@ -290,11 +287,9 @@ struct RowsLoop {
   int* s_abort;
   Status* status;
   int x0, ylo, nstage, ring;
-  int issued = 0;  // rows the staging warp has issued (staging warp only)
   C Uwall;
   const C* body;     // Kolmogorov body acceleration per row (BODY only; nullptr: none)
   const Series& sr;  // shear-response record (sr.buf == nullptr: off)
-  long long wait_limit;  // bound of the compute warps' waits for a staged row (cycles)
   C sacc;            // this thread's sum of u_x sin(k y) over its collided sites
   const C* swt;      // the record's row weights (nullptr: no record), kept in registers
   // this thread (a compute thread serves column x = x0 + t)
@@ -331,10 +326,10 @@ struct RowsLoop {
                                       const Geom& g_, const Phys<C>& ph_, C Uwall_,
                                       const C* body_, int x0_, int x1, int ylo_, int yhi,
                                       const RowsSmem<STORAGE>& sm_, int ring_, int* s_abort_,
-                                      Status* status_, const Series& sr_, long long wait_limit_)
+                                      Status* status_, const Series& sr_)
       : src(src_), g(g_), ph(ph_), sm(sm_), s_abort(s_abort_), status(status_), x0(x0_),
         ylo(ylo_), nstage((yhi - ylo_) + 4), ring(ring_), Uwall(Uwall_), body(body_), sr(sr_),
-        wait_limit(wait_limit_), sacc(C(0)), swt(sr_.buf ? (const C*)sr_.wt : nullptr) {
+        sacc(C(0)), swt(sr_.buf ? (const C*)sr_.wt : nullptr) {
     warp = threadIdx.x >> 5;
     lane = threadIdx.x & 31;
     t = (warp < NCW) ? (int)threadIdx.x : 0;
@@ -372,10 +367,18 @@ struct RowsLoop {
   __device__ __forceinline__ uint32_t round_of(int j) const { return (uint32_t)((ring + j) / NSLOT); }
 
   // ---- the staging warp: stage rows 0 .. nstage-1, each into a slot that
-  // every compute warp has released ----
-  __device__ __forceinline__ void produce() {
+  // every compute warp has released.  `stall` (a test hook for the timeout
+  // path) issues no copy at all, so that the compute warps' first wait runs
+  // out.  Before it leaves, the warp waits (bounded) for the copies it issued
+  // that may still be landing -- after an abort nothing else would, and no
+  // copy may write into this CTA's shared memory once it moves on or exits.
+  // Only the last NSLOT issued rows can be in flight (a slot is refilled only
+  // after its row was consumed); in a range that ran to the end they have
+  // landed or land within the compute warps' last rows. ----
+  __device__ __forceinline__ void produce(int stall) {
+    const int n = stall ? 0 : nstage;
     int j = 0;
-    for (; j < nstage; ++j) {
+    for (; j < n; ++j) {
       const int s = slot_of(j);
       const uint32_t rnd = round_of(j);
       if (rnd > 0 && !mbar_wait_backoff(&sm.empty[s], (rnd - 1) & 1, s_abort)) {
@@ -388,7 +391,14 @@ struct RowsLoop {
       if (*(volatile int*)s_abort) break;
       issue_row<STORAGE>(src, sm.stage + s * SLOT, &sm.full[s], g, x0, ylo - 2 + j, lane);
     }
-    issued = j;
+    if (lane == 0) {
+      for (int k = (j > NSLOT ? j - NSLOT : 0); k < j; ++k) {
+        const long long t0 = clock64();
+        while (!mbar_try_wait(&sm.full[slot_of(k)], round_of(k) & 1))
+          if (clock64() - t0 > kWaitLimitDefault) break;
+      }
+    }
+    __syncwarp();
   }
 
   // rho, drho and psi pairs of staged column c (0 .. SW-1) of a staged row
@@ -543,13 +553,9 @@ struct RowsLoop {
       atomicAdd(&sr.buf[sr.step % sr.cap], v);
   }
 
-  // Wait for staged row j.  Under the test hook (a bound shorter than the
-  // default) the warp waits on a barrier that nothing completes instead, so
-  // that the bound, not the copy, ends the wait.
+  // Wait for staged row j.
   __device__ __forceinline__ bool wait_row(int j) {
-    const bool hook = wait_limit < kWaitLimitDefault;
-    if (!mbar_wait_bounded(hook ? sm.never : &sm.full[slot_of(j)], hook ? 0u : round_of(j) & 1,
-                           wait_limit)) {
+    if (!mbar_wait_bounded(&sm.full[slot_of(j)], round_of(j) & 1)) {
       if (lane == 0) {
         atomicExch(&status->timeout, 1u);
         *s_abort = 1;
@@ -815,29 +821,12 @@ struct RowsLoop {
 
 };
 
-// After an abort (one thread of the staging warp, once every warp of the CTA
-// has left the range): wait, bounded, for the copies still in flight, so that
-// none is writing into this CTA's shared memory when it moves on or exits.
-// Rows ring0 .. ring0 + issued - 1 of the slot ring were issued; only the last
-// NSLOT can be outstanding (a slot is refilled only after its row was consumed).
-template <int STORAGE>
-__device__ __noinline__ void drain_copies(const RowsSmem<STORAGE>& sm, int ring0, int issued) {
-  constexpr int NSLOT = RowsCfg<STORAGE>::NSLOT;
-  for (int k = (issued > NSLOT ? issued - NSLOT : 0); k < issued; ++k) {
-    const int j = ring0 + k;
-    const long long t0 = clock64();
-    while (!mbar_try_wait(&sm.full[j % NSLOT], (uint32_t)(j / NSLOT) & 1)) {
-      if (clock64() - t0 > kWaitLimitDefault) break;
-    }
-  }
-}
-
 // One CTA, one work range: columns x0 .. x1-1 (at most RX), output rows
 // ylo .. yhi-1 of the lattice (src -> dst).  `ring` is the position of the
 // next staged row in the CTA's slot ring (identical in every thread); on
 // entry every slot is free or will be released by the compute warps.  A
-// bounded wait that gives up raises *s_abort (read it after a __syncthreads);
-// every thread of the CTA calls this (it ends with a CTA barrier).
+// bounded wait that gives up raises *s_abort (read it after a __syncthreads).
+// `stall`: the staging warp's test hook (see RowsLoop::produce).
 template <int STORAGE, bool BODY, bool LAG = RowsCfg<STORAGE>::LAG>
 __device__ __forceinline__ void rows_range(
     const typename PairStore<STORAGE>::T2* __restrict__ src,
@@ -845,26 +834,15 @@ __device__ __forceinline__ void rows_range(
     const Phys<typename Store<STORAGE>::C>& ph, typename Store<STORAGE>::C Uwall,
     const typename Store<STORAGE>::C* body, int x0, int x1, int ylo, int yhi,
     const RowsSmem<STORAGE>& sm, int& ring, int* s_abort, Status* status, int& bad,
-    const Series& sr, long long wait_limit) {
-  const int ring0 = ring;
-  int issued = 0;
-  {
-    RowsLoop<STORAGE, BODY, LAG> L(src, dst, g, ph, Uwall, body, x0, x1, ylo, yhi, sm, ring,
-                                   s_abort, status, sr, wait_limit);
-    if (L.warp == RowsCfg<STORAGE>::NCW) {
-      L.produce();
-      issued = L.issued;
-    } else {
-      L.consume();
-    }
-    bad += L.bad;
-  }
-  ring += (yhi - ylo) + 4;
-  // every warp has left the range: after an abort the staging warp waits for
-  // the copies it issued that may still be landing
-  __syncthreads();
-  if (*(volatile int*)s_abort && threadIdx.x == 32 * RowsCfg<STORAGE>::NCW)
-    drain_copies<STORAGE>(sm, ring0, issued);
+    const Series& sr, int stall) {
+  RowsLoop<STORAGE, BODY, LAG> L(src, dst, g, ph, Uwall, body, x0, x1, ylo, yhi, sm, ring,
+                                 s_abort, status, sr);
+  if (L.warp == RowsCfg<STORAGE>::NCW)
+    L.produce(stall);
+  else
+    L.consume();
+  bad += L.bad;
+  ring += L.nstage;
 }
 
 // Resident CTAs per SM of a kernel variant at the row kernels' shared memory.

@@ -57,12 +57,13 @@ int rows_batch_grid(int storage);
 
 // `body`: the Kolmogorov body acceleration of every row, ny values of the
 // storage's arithmetic type (float, or double for FP64), or nullptr.
-// `wait_limit`: bound (SM cycles) of the compute warps' waits for a staged row;
-// kWaitLimitDefault unless a test shortens it to exercise the timeout path.
-constexpr long long kWaitLimitDefault = 1LL << 31;
+// `stall`: 0, or (a test hook for the timeout path) nonzero: the staging warps
+// issue no copy, so the compute warps' waits for a staged row run out after
+// kWaitLimitDefault cycles and the step reports a timeout.
+constexpr long long kWaitLimitDefault = 1LL << 31;  // bound of every mbarrier wait (SM cycles)
 cudaError_t launch_step_rows(int storage, const void* src, void* dst, const Geom& g,
                              const PhysD& ph, const void* body, Status* status, const Series& sr,
-                             long long wait_limit, cudaStream_t st);
+                             int stall, cudaStream_t st);
 
 // Device table of the Kolmogorov body acceleration g sin(2 pi k y / ny), y in
 // [0, ny), in the arithmetic type of `storage` (cudaMalloc'd; nullptr when g = 0).
@@ -77,7 +78,7 @@ cudaError_t make_body_table(int storage, const PhysD& ph, int ny, void** out, cu
 // replica keeps a shear-response record.
 cudaError_t launch_step_rows_batch(int storage, void* reps, const WorkItem* items,
                                    const int* offsets, int grid, const void* table, int nphys,
-                                   bool body, bool rec, Status* status, long long wait_limit,
+                                   bool body, bool rec, Status* status, int stall,
                                    cudaStream_t st);
 
 }  // namespace lbk

@@ -21,7 +21,7 @@ template <int STORAGE, bool ONE, int MODE>
 __global__ void __launch_bounds__(cta_threads<STORAGE>(), RowsCfg<STORAGE>::MINB)
     k_rows_batch(ReplicaDev<typename Store<STORAGE>::C>* __restrict__ reps,
                  const WorkItem* __restrict__ items, const int* __restrict__ offsets,
-                 Status* status, long long wait_limit,
+                 Status* status, int stall,
                  const __grid_constant__ PhysTable<typename Store<STORAGE>::C> tab) {
   using T2 = typename PairStore<STORAGE>::T2;
   using C = typename Store<STORAGE>::C;
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(cta_threads<STORAGE>(), RowsCfg<STORAGE>::MINB
     const Series none{};
     rows_range<STORAGE, (MODE > 0), RowsCfg<STORAGE>::LAG_BATCH>(s_src, s_dst, s_g, tab.p[ONE ? 0 : s_phys], s_U, s_body,
                                     s_item.x0, s_item.x1, s_item.ylo, s_item.yhi, sm, ring,
-                                    &s_abort, status, bad, MODE == 2 ? s_sr : none, wait_limit);
+                                    &s_abort, status, bad, MODE == 2 ? s_sr : none, stall);
     __syncthreads();
     if (s_abort) break;
     if (threadIdx.x == 0) {
@@ -123,7 +123,7 @@ int rows_batch_grid(int storage) {
 
 template <int STORAGE, bool ONE>
 static cudaError_t rows_batch_v(void* reps, const WorkItem* items, const int* offsets, int grid,
-                                const void* table, int mode, Status* status, long long wait_limit,
+                                const void* table, int mode, Status* status, int stall,
                                 cudaStream_t st) {
   using C = typename Store<STORAGE>::C;
   auto* R = (ReplicaDev<C>*)reps;
@@ -133,43 +133,43 @@ static cudaError_t rows_batch_v(void* reps, const WorkItem* items, const int* of
   // (an ordinary launch: the batched step is long, see launch_step_kernel)
   if (mode == 2)
     return launch_step_kernel(false, k_rows_batch<STORAGE, ONE, 2>, grid, th, smem, st, R, items,
-                              offsets, status, wait_limit, tab);
+                              offsets, status, stall, tab);
   if (mode == 1)
     return launch_step_kernel(false, k_rows_batch<STORAGE, ONE, 1>, grid, th, smem, st, R, items,
-                              offsets, status, wait_limit, tab);
+                              offsets, status, stall, tab);
   return launch_step_kernel(false, k_rows_batch<STORAGE, ONE, 0>, grid, th, smem, st, R, items,
-                            offsets, status, wait_limit, tab);
+                            offsets, status, stall, tab);
 }
 
 template <int STORAGE>
 static cudaError_t rows_batch_t(void* reps, const WorkItem* items, const int* offsets, int grid,
                                 const void* table, int nphys, bool body, bool rec,
-                                Status* status, long long wait_limit, cudaStream_t st) {
+                                Status* status, int stall, cudaStream_t st) {
   const int mode = rec ? 2 : (body ? 1 : 0);
   if (nphys <= 1)
-    return rows_batch_v<STORAGE, true>(reps, items, offsets, grid, table, mode, status, wait_limit,
+    return rows_batch_v<STORAGE, true>(reps, items, offsets, grid, table, mode, status, stall,
                                        st);
-  return rows_batch_v<STORAGE, false>(reps, items, offsets, grid, table, mode, status, wait_limit,
+  return rows_batch_v<STORAGE, false>(reps, items, offsets, grid, table, mode, status, stall,
                                       st);
 }
 
 cudaError_t launch_step_rows_batch(int storage, void* reps, const WorkItem* items,
                                    const int* offsets, int grid, const void* table, int nphys,
-                                   bool body, bool rec, Status* status, long long wait_limit,
+                                   bool body, bool rec, Status* status, int stall,
                                    cudaStream_t st) {
   switch (storage) {
     case LB_F64:
       return rows_batch_t<LB_F64>(reps, items, offsets, grid, table, nphys, body, rec, status,
-                                  wait_limit, st);
+                                  stall, st);
     case LB_F32:
       return rows_batch_t<LB_F32>(reps, items, offsets, grid, table, nphys, body, rec, status,
-                                  wait_limit, st);
+                                  stall, st);
     case LB_BF16_DEV:
       return rows_batch_t<LB_BF16_DEV>(reps, items, offsets, grid, table, nphys, body, rec, status,
-                                       wait_limit, st);
+                                       stall, st);
     case LB_F16_DEV:
       return rows_batch_t<LB_F16_DEV>(reps, items, offsets, grid, table, nphys, body, rec, status,
-                                      wait_limit, st);
+                                      stall, st);
   }
   return cudaErrorInvalidValue;
 }
