@@ -398,7 +398,8 @@ def single_lattice(lb, D, name, steps, warmup, seed, reps=25, target_s=1.5, cloc
            "ms_per_step": med / steps, "blocks": len(ms), "steps_per_block": steps,
            "ms_block_min_max": [min(ms), max(ms)], "bytes_per_site": bps,
            "achieved_gbs": achieved, "frac": achieved / peak, "peak_gbs": peak,
-           "peak_kind": peak_kind, "status": lb.lb_strerror(lat.status())}
+           "peak_kind": peak_kind, "status": lb.lb_strerror(lat.status()),
+           "row_shape": lat.row_shape}
     return out, lat, stream
 
 
@@ -494,7 +495,11 @@ def run_gpu(args):
                            "l2": f"inputs larger than L2 ({lb.lb_state_bytes(nx, ny, storage) / 1e9:.2f} GB per buffer)",
                            "timing": f"median of {res['blocks']} timed blocks of {args.steps} "
                                      "graph-replayed steps, each between barriers",
-                           "parallelism": f"replicas{world}"},
+                           "parallelism": f"replicas{world}",
+                           "row_shape": res["row_shape"],
+                           "row_shape_choice": ("timed at lb_create (lb_autotune, 8 steps "
+                                                "per candidate)")
+                           if storage == 1 and sites >= 1 << 22 else "default"},
                 "roofline": roof,
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": "MLUPS",

@@ -141,6 +141,26 @@ LB_API int lb_init_random(lb_handle *h, uint64_t seed);
  * when n is large).  Errors met on the device are reported by lb_status(). */
 LB_API int lb_step(lb_handle *h, int64_t n);
 
+/* CTA shape of the row-streaming step kernel: 0 (every storage: 4 compute
+ * warps on 128-column strips) or 1 (FP32 only: 7 compute warps on 224-column
+ * strips, two CTAs per SM -- fewer halo columns per site, faster on large
+ * lattices, slower on small ones); -1 when the lattice is stepped by the
+ * generic tile kernel.  The shape changes how the lattice is cut into CTA
+ * work, not the arithmetic: every shape gives the same bits.  lb_create()
+ * chooses it by timing the candidates (lb_autotune with 8 steps each) on
+ * FP32 lattices of at least 2^22 sites, else takes shape 0; the environment
+ * variable LB_ROW_SHAPE=0|1, read by lb_create(), forces one (LB_EINVAL if
+ * it does not apply). */
+LB_API int lb_row_shape(const lb_handle *h);
+
+/* Time each available row-kernel shape for steps_per_candidate >= 1 steps
+ * (after two untimed ones) and keep the fastest; another shape replaces the
+ * current one only if it is at least 1 % faster.  The candidates step from
+ * the current state into the handle's other buffer, so the state, the step
+ * count and the status word are unchanged.  Synchronises.  *shape (may be
+ * NULL) receives the choice.  A lattice with one candidate returns at once. */
+LB_API int lb_autotune(lb_handle *h, int steps_per_candidate, int *shape);
+
 /* Observables of the current state f(t), FP64 on the device; synchronises.
  * Any pointer may be NULL to skip that output.
  *   rho[2*ny*nx]  species densities rho_s = sum_i f_is, layout [s][y][x];

@@ -38,6 +38,7 @@ struct lb_handle {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int graph_steps = 0;
   int use_rows = 0;       // 1 if the row-streaming kernel serves this lattice
+  int shape = 0;          // its CTA shape (lb_row_shape)
   int stall = 0;  // the row kernel's timeout test hook (stall_from_env)
   Series sr{nullptr, nullptr, nullptr, 0, 0, 0u};  // shear-response record (off by default)
 };
@@ -137,6 +138,25 @@ static int create_common(int nx, int ny, const lb_params* p, void* stream, void*
     h->use_rows = 1;
   } else
     h->use_rows = (rows_ok && nx >= 128) ? 1 : 0;
+  // the row kernel's CTA shape: LB_ROW_SHAPE forces one; large FP32 lattices
+  // time the candidates on the zeroed buffers (deviation storage: the uniform
+  // rest state rho_ref, no non-positive densities)
+  const char* shape = getenv("LB_ROW_SHAPE");
+  if (shape && *shape) {
+    h->shape = atoi(shape);
+    if (!h->use_rows || h->shape < 0 || h->shape >= kRowShapes ||
+        !rows_shape_available(p->storage, h->shape)) {
+      lb_destroy(h);
+      return LB_EINVAL;
+    }
+  } else if (h->use_rows && !h->stall && p->storage == LB_F32 &&
+             (long long)nx * ny >= (1LL << 22)) {
+    rc = lb_autotune(h, 8, nullptr);
+    if (rc) {
+      lb_destroy(h);
+      return rc;
+    }
+  }
   *out = h;
   return LB_OK;
 }
@@ -195,8 +215,8 @@ static cudaError_t step_once(lb_handle* h, int from, cudaStream_t st) {
   const void* src = h->buf[from];
   void* dst = h->buf[1 - from];
   if (h->use_rows)
-    return launch_step_rows(h->p.storage, src, dst, h->g, h->ph, h->d_body, h->d_status, h->sr,
-                            h->stall, st);
+    return launch_step_rows(h->p.storage, h->shape, src, dst, h->g, h->ph, h->d_body,
+                            h->d_status, h->sr, h->stall, st);
   return launch_step_tile(h->p.storage, src, dst, h->g, h->ph, h->d_status, h->sr, st);
 }
 
@@ -229,6 +249,73 @@ static int ensure_graph(lb_handle* h, int from) {
     return LB_ECUDA;
   }
   h->graph_steps = kGraphSteps;
+  return LB_OK;
+}
+
+extern "C" int lb_row_shape(const lb_handle* h) {
+  if (!h) return -1;
+  return h->use_rows ? h->shape : -1;
+}
+
+extern "C" int lb_autotune(lb_handle* h, int steps_per_candidate, int* shape_out) {
+  if (!h || steps_per_candidate < 1) return LB_EINVAL;
+  if (shape_out) *shape_out = lb_row_shape(h);
+  if (!h->use_rows) return LB_OK;
+  int cand[kRowShapes], nc = 0;
+  for (int s = 0; s < kRowShapes; ++s)
+    if (rows_shape_available(h->p.storage, s)) cand[nc++] = s;
+  if (nc < 2) return LB_OK;
+  // the status word is kept: read it, and write it back after the candidates
+  Status saved;
+  if (cudaMemcpyAsync(&saved, h->d_status, sizeof(Status), cudaMemcpyDeviceToHost, h->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return LB_ECUDA;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    cudaGetLastError();
+    return LB_ECUDA;
+  }
+  const int keep = h->shape;
+  const Series keep_sr = h->sr;
+  h->sr.buf = nullptr;  // (the candidates' steps are not recorded)
+  float ms[kRowShapes] = {};
+  int rc = LB_OK;
+  for (int c = 0; c < nc && rc == LB_OK; ++c) {
+    h->shape = cand[c];
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = step_once(h, h->cur, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+    for (int k = 0; k < steps_per_candidate && e == cudaSuccess; ++k)
+      e = step_once(h, h->cur, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[c], e0, e1);
+    if (e != cudaSuccess) rc = LB_ECUDA;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->shape = keep;
+  h->sr = keep_sr;
+  if (rc) {
+    cudaGetLastError();
+    return rc;
+  }
+  int best = -1;
+  for (int c = 0; c < nc; ++c)
+    if (cand[c] == keep) best = c;
+  for (int c = 0; c < nc; ++c)
+    if (ms[c] < 0.99f * ms[best]) best = c;
+  if (cand[best] != h->shape) {
+    drop_graphs(h);  // (captured with the previous shape)
+    h->shape = cand[best];
+  }
+  if (cudaMemcpyAsync(h->d_status, &saved, sizeof(Status), cudaMemcpyHostToDevice, h->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return LB_ECUDA;
+  if (shape_out) *shape_out = h->shape;
   return LB_OK;
 }
 

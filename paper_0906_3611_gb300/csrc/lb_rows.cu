@@ -15,9 +15,9 @@ namespace lbk {
 // step carries none of their code or registers.
 template <int STORAGE, int MODE>
 __global__ void __launch_bounds__(cta_threads<STORAGE>(), RowsCfg<STORAGE>::MINB)
-    k_rows(const typename PairStore<STORAGE>::T2* __restrict__ src,
-           typename PairStore<STORAGE>::T2* __restrict__ dst, Geom g,
-           Phys<typename Store<STORAGE>::C> ph, const typename Store<STORAGE>::C* body,
+    k_rows(const typename PairStore<row_storage(STORAGE)>::T2* __restrict__ src,
+           typename PairStore<row_storage(STORAGE)>::T2* __restrict__ dst, Geom g,
+           Phys<typename Store<row_storage(STORAGE)>::C> ph, const typename Store<row_storage(STORAGE)>::C* body,
            int nstrips, int kranges, Status* status, Series sr, int stall) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_abort;
@@ -62,7 +62,9 @@ static int resident_blocks() {
   return cached;
 }
 
-static int resident(int storage) {
+static int resident(int storage, int shape = 0) {
+  if (shape == 1) return storage == LB_F32 ? resident_blocks<row_key(LB_F32, 1)>() : 0;
+  if (shape != 0) return 0;
   switch (storage) {
     case LB_F64: return resident_blocks<LB_F64>();
     case LB_F32: return resident_blocks<LB_F32>();
@@ -70,6 +72,11 @@ static int resident(int storage) {
     case LB_F16_DEV: return resident_blocks<LB_F16_DEV>();
   }
   return 0;
+}
+
+bool rows_shape_available(int storage, int shape) {
+  // (also sets the shape's shared-memory attributes, outside any stream capture)
+  return resident(storage, shape) > 0;
 }
 
 int rows_strip_width(int storage) {
@@ -126,11 +133,11 @@ template <int STORAGE>
 static cudaError_t rows_t(const void* src, void* dst, const Geom& g, const PhysD& pd,
                           const void* body_v, Status* status, const Series& sr_in,
                           int stall, cudaStream_t st) {
-  using C = typename Store<STORAGE>::C;
+  using C = typename Store<row_storage(STORAGE)>::C;
   const C* body = (const C*)body_v;
-  using T2 = typename PairStore<STORAGE>::T2;
+  using T2 = typename PairStore<row_storage(STORAGE)>::T2;
   const int nstrips = rows_nstrips(g.nx, strip_cols<STORAGE>());
-  int k = resident(STORAGE) / nstrips;
+  int k = resident(row_storage(STORAGE), STORAGE >> 2) / nstrips;
   if (k < 1) k = 1;
   if (k > g.ny) k = g.ny;
   const size_t smem = rows_smem_bytes<STORAGE>();
@@ -151,9 +158,14 @@ static cudaError_t rows_t(const void* src, void* dst, const Geom& g, const PhysD
                             nstrips, k, status, sr, stall);
 }
 
-cudaError_t launch_step_rows(int storage, const void* src, void* dst, const Geom& g,
+cudaError_t launch_step_rows(int storage, int shape, const void* src, void* dst, const Geom& g,
                              const PhysD& ph, const void* body, Status* status, const Series& sr,
                              int stall, cudaStream_t st) {
+  if (shape == 1) {
+    if (storage != LB_F32) return cudaErrorInvalidValue;
+    return rows_t<row_key(LB_F32, 1)>(src, dst, g, ph, body, status, sr, stall, st);
+  }
+  if (shape != 0) return cudaErrorInvalidValue;
   switch (storage) {
     case LB_F64: return rows_t<LB_F64>(src, dst, g, ph, body, status, sr, stall, st);
     case LB_F32: return rows_t<LB_F32>(src, dst, g, ph, body, status, sr, stall, st);

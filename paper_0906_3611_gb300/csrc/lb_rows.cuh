@@ -71,6 +71,14 @@ struct RowsCfg<LB_F32> {
   static constexpr int NCW = 4, SOFF = 2, NSLOT = 7, MINB = 3;  // 8-byte pairs
   static constexpr bool PIPE = true, LAG = true, LAG_BATCH = true, CPAR = false;
 };
+// the wide FP32 shape: 7 compute warps on 224-column strips, 2 CTAs per SM
+// (4 halo columns per 224 instead of per 128; the ring is one slot shorter
+// so that two CTAs fit the shared memory)
+template <>
+struct RowsCfg<row_key(LB_F32, 1)> {
+  static constexpr int NCW = 7, SOFF = 2, NSLOT = 6, MINB = 2;
+  static constexpr bool PIPE = true, LAG = true, LAG_BATCH = true, CPAR = false;
+};
 template <>
 struct RowsCfg<LB_BF16_DEV> {
   static constexpr int NCW = 4, SOFF = 4, NSLOT = 8, MINB = 4;  // 4-byte pairs
@@ -97,8 +105,8 @@ constexpr int stage_width() {
 
 template <int STORAGE>
 constexpr size_t rows_smem_bytes() {
-  using T2 = typename PairStore<STORAGE>::T2;
-  using P = typename PairOf<typename Store<STORAGE>::C>::P;
+  using T2 = typename PairStore<row_storage(STORAGE)>::T2;
+  using P = typename PairOf<typename Store<row_storage(STORAGE)>::C>::P;
   return (size_t)RowsCfg<STORAGE>::NSLOT * 9 * stage_width<STORAGE>() * sizeof(T2) +
          (size_t)RowsCfg<STORAGE>::NCW * 2 * WEXT * sizeof(P) + 2 * RowsCfg<STORAGE>::NSLOT * 8;
 }
@@ -211,10 +219,10 @@ __device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, u
 // as one bulk copy per contiguous run of the periodic window (one run, or two
 // across the seam; more only for lattices narrower than the window).
 template <int STORAGE>
-__device__ __forceinline__ void issue_row(const typename PairStore<STORAGE>::T2* __restrict__ src,
-                                          typename PairStore<STORAGE>::T2* slot, uint64_t* bar,
+__device__ __forceinline__ void issue_row(const typename PairStore<row_storage(STORAGE)>::T2* __restrict__ src,
+                                          typename PairStore<row_storage(STORAGE)>::T2* slot, uint64_t* bar,
                                           const Geom& g, int x0, int r, int lane) {
-  using T2 = typename PairStore<STORAGE>::T2;
+  using T2 = typename PairStore<row_storage(STORAGE)>::T2;
   constexpr int SOFF = RowsCfg<STORAGE>::SOFF;
   constexpr int SW = stage_width<STORAGE>();
   if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(9 * SW * sizeof(T2)));
@@ -236,8 +244,8 @@ __device__ __forceinline__ void issue_row(const typename PairStore<STORAGE>::T2*
 // Shared-memory layout of a CTA.
 template <int STORAGE>
 struct RowsSmem {
-  using T2 = typename PairStore<STORAGE>::T2;
-  using P = typename PairOf<typename Store<STORAGE>::C>::P;
+  using T2 = typename PairStore<row_storage(STORAGE)>::T2;
+  using P = typename PairOf<typename Store<row_storage(STORAGE)>::C>::P;
   static constexpr int NSLOT = RowsCfg<STORAGE>::NSLOT;
   static constexpr int NCW = RowsCfg<STORAGE>::NCW;
   static constexpr int SLOT = 9 * stage_width<STORAGE>();
@@ -270,9 +278,9 @@ struct RowsSmem {
 // specialised per rotation; staging and collision are shared).
 template <int STORAGE, bool BODY, bool LAG = RowsCfg<STORAGE>::LAG>
 struct RowsLoop {
-  using PS = PairStore<STORAGE>;
+  using PS = PairStore<row_storage(STORAGE)>;
   using T2 = typename PS::T2;
-  using C = typename Store<STORAGE>::C;
+  using C = typename Store<row_storage(STORAGE)>::C;
   using P = typename PairOf<C>::P;
   static constexpr int SOFF = RowsCfg<STORAGE>::SOFF;
   static constexpr int NSLOT = RowsCfg<STORAGE>::NSLOT;
@@ -756,7 +764,7 @@ struct RowsLoop {
       d[8] = pfma(keep, d[8], padd(e2, ad2));
       d[6] = pfma(keep, d[6], psub(e2, ad2));
     }
-    if (STORAGE != LB_F64) {
+    if (row_storage(STORAGE) != LB_F64) {
       // mass-exact rest population: the collision conserves rho_s exactly,
       // so give the rest population what the eight moving ones (as stored)
       // leave of drho; one rounding per site instead of a biased sum of nine
@@ -804,7 +812,7 @@ struct RowsLoop {
           d[i] = pfma(pbc(-C(6) * wq<C>(i) * C(Q9::cx(i)) * Uw), rho, d[i]);
         }
       }
-      if (STORAGE != LB_F64)  // mass-exact again, with the values the wall sends back
+      if (row_storage(STORAGE) != LB_F64)  // mass-exact again, with the values the wall sends back
         d[0] = psub(drho, stored_sum8(d));
 #pragma unroll
       for (int i = 0; i < 9; ++i) {
@@ -829,10 +837,10 @@ struct RowsLoop {
 // `stall`: the staging warp's test hook (see RowsLoop::produce).
 template <int STORAGE, bool BODY, bool LAG = RowsCfg<STORAGE>::LAG>
 __device__ __forceinline__ void rows_range(
-    const typename PairStore<STORAGE>::T2* __restrict__ src,
-    typename PairStore<STORAGE>::T2* __restrict__ dst, const Geom& g,
-    const Phys<typename Store<STORAGE>::C>& ph, typename Store<STORAGE>::C Uwall,
-    const typename Store<STORAGE>::C* body, int x0, int x1, int ylo, int yhi,
+    const typename PairStore<row_storage(STORAGE)>::T2* __restrict__ src,
+    typename PairStore<row_storage(STORAGE)>::T2* __restrict__ dst, const Geom& g,
+    const Phys<typename Store<row_storage(STORAGE)>::C>& ph, typename Store<row_storage(STORAGE)>::C Uwall,
+    const typename Store<row_storage(STORAGE)>::C* body, int x0, int x1, int ylo, int yhi,
     const RowsSmem<STORAGE>& sm, int& ring, int* s_abort, Status* status, int& bad,
     const Series& sr, int stall) {
   RowsLoop<STORAGE, BODY, LAG> L(src, dst, g, ph, Uwall, body, x0, x1, ylo, yhi, sm, ring,

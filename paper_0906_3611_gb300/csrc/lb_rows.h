@@ -36,8 +36,19 @@ struct WorkItem {
   int replica, x0, x1, ylo, yhi;
 };
 
-// Columns per strip of the row-streaming kernels for a storage (32 per
-// compute warp of a CTA).
+// CTA shapes of the single-lattice row kernel.  Shape 0 is every storage's
+// default: 4 compute warps on 128-column strips.  Shape 1, FP32 only: 7
+// compute warps on 224-column strips, 2 CTAs per SM instead of 3 (fewer halo
+// columns per site: faster on large lattices, slower on small ones).  Kernel
+// instantiations are keyed by storage | shape << 2.
+constexpr int kRowShapes = 2;
+constexpr int row_key(int storage, int shape) { return storage | (shape << 2); }
+constexpr int row_storage(int key) { return key & 3; }
+// True if the shape exists for the storage and its kernels fit this device.
+bool rows_shape_available(int storage, int shape);
+
+// Columns per strip of the row-streaming kernels for a storage, shape 0 (32
+// per compute warp of a CTA).
 int rows_strip_width(int storage);
 
 // Strips of a lattice row: `width` columns (the last one ragged).
@@ -61,7 +72,7 @@ int rows_batch_grid(int storage);
 // issue no copy, so the compute warps' waits for a staged row run out after
 // kWaitLimitDefault cycles and the step reports a timeout.
 constexpr long long kWaitLimitDefault = 1LL << 31;  // bound of every mbarrier wait (SM cycles)
-cudaError_t launch_step_rows(int storage, const void* src, void* dst, const Geom& g,
+cudaError_t launch_step_rows(int storage, int shape, const void* src, void* dst, const Geom& g,
                              const PhysD& ph, const void* body, Status* status, const Series& sr,
                              int stall, cudaStream_t st);
 

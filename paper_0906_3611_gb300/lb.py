@@ -24,6 +24,7 @@ ELEM_BYTES = {LB_F64: 8, LB_F32: 4, LB_BF16_DEV: 2, LB_F16_DEV: 2}
 
 # every entry point declared in include/lb.h
 EXPORTED = ["lb_state_bytes", "lb_create", "lb_create_on", "lb_init_random", "lb_step",
+            "lb_row_shape", "lb_autotune",
             "lb_observables", "lb_shear_diagnostics", "lb_series_start", "lb_series_read",
             "lb_series_stop", "lb_series_bursts", "lb_batch_series_bursts", "lb_phi_snapshot", "lb_phi_overlap",
             "lb_get_state", "lb_set_state",
@@ -78,6 +79,8 @@ def _load():
         "lb_create_on": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, pp, vp, vp, vp, ctypes.c_size_t, hp]),
         "lb_init_random": (ctypes.c_int, [vp, ctypes.c_uint64]),
         "lb_step": (ctypes.c_int, [vp, ctypes.c_int64]),
+        "lb_row_shape": (ctypes.c_int, [vp]),
+        "lb_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "lb_observables": (ctypes.c_int, [vp, dp, dp, dp, dp]),
         "lb_shear_diagnostics": (ctypes.c_int, [vp, dp, dp]),
         "lb_series_start": (ctypes.c_int, [vp, ctypes.c_int64]),
@@ -289,6 +292,16 @@ def lb_get_state_raw(h: int, ptr: int) -> None:
     _check(_lib.lb_get_state_raw(h, ctypes.c_void_p(ptr)), "lb_get_state_raw")
 
 
+def lb_row_shape(h: int) -> int:
+    return int(_lib.lb_row_shape(h))
+
+
+def lb_autotune(h: int, steps_per_candidate: int) -> int:
+    shape = ctypes.c_int(-1)
+    _check(_lib.lb_autotune(h, steps_per_candidate, ctypes.byref(shape)), "lb_autotune")
+    return shape.value
+
+
 def lb_time(h: int) -> int:
     return int(_lib.lb_time(h))
 
@@ -443,6 +456,15 @@ class Lattice:
     def step(self, n: int = 1):
         lb_step(self.h, n)
         return self
+
+    @property
+    def row_shape(self) -> int:
+        """CTA shape of the row kernel (0, 1), -1 for the tile kernel."""
+        return lb_row_shape(self.h)
+
+    def autotune(self, steps_per_candidate: int = 8) -> int:
+        """Time the row-kernel shapes and keep the fastest (state unchanged)."""
+        return lb_autotune(self.h, steps_per_candidate)
 
     def series_start(self, capacity: int):
         """Record U_k after every step (device ring of `capacity` entries)."""

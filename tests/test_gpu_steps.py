@@ -1,4 +1,4 @@
-"""The three ways a lattice is stepped agree bit for bit.
+"""The ways a lattice is stepped agree bit for bit.
 
 A lattice stepped n times in one call replays captured graphs of 32 steps
 and launches the rest one by one; stepped one step per call, it launches
@@ -6,7 +6,10 @@ every step alone; run as a batch replica, it goes through the batched
 kernel, which splits the rows into other work items.  The per-site
 arithmetic does not depend on any of this, so all three must agree bit for
 bit, across graph boundaries, odd step counts and the buffer parity they
-leave, in every storage and for both boundaries.
+leave, in every storage and for both boundaries.  The FP32 row kernel's two
+CTA shapes cut the lattice into different strips and ranges and give the
+same bits too; the shape autotuner leaves the state, the step count and the
+status word as they were.
 """
 import numpy as np
 import pytest
@@ -57,3 +60,50 @@ def test_one_call_equals_single_steps_and_the_batched_kernel(lb, monkeypatch, st
     assert bt.status() == lb.LB_OK
     bt.close()
     assert np.array_equal(fa, fc)
+
+
+@pytest.mark.parametrize("boundary", [0, 1], ids=["periodic", "couette"])
+@pytest.mark.parametrize("nx", [500, 1024])
+def test_the_wide_cta_shape_gives_the_same_bits(lb, monkeypatch, nx, boundary):
+    # FP32 shape 1 (224-column strips, 7 compute warps) against shape 0
+    # (128-column strips); nx = 500 leaves a ragged last strip in both
+    p = _p(lb, lb.LB_F32, boundary)
+    ny, n = 96, 45
+    out = []
+    for shape in ("0", "1"):
+        monkeypatch.setenv("LB_ROW_SHAPE", shape)
+        lat = lb.Lattice(nx, ny, p)
+        assert lat.row_shape == int(shape)
+        out.append(lat.init_random(8).step(n).get_state())
+        assert lat.status() == lb.LB_OK
+        lat.close()
+    assert np.array_equal(out[0], out[1])
+
+
+def test_autotune_keeps_the_state_and_reports_the_shape(lb, monkeypatch):
+    monkeypatch.setenv("LB_STEP_KERNEL", "rows")
+    p = _p(lb, lb.LB_F32, 1)
+    a = lb.Lattice(640, 200, p).init_random(4).step(9)
+    f = a.get_state()
+    shape = a.autotune(3)
+    assert shape in (0, 1) and a.row_shape == shape
+    assert np.array_equal(a.get_state(), f)
+    assert a.time == 9 and a.status() == lb.LB_OK
+    g = a.step(30).get_state()
+    b = lb.Lattice(640, 200, p).init_random(4).step(39)
+    assert np.array_equal(b.get_state(), g)
+    a.close()
+    b.close()
+
+
+def test_shape_forcing_and_the_tile_kernel(lb, monkeypatch):
+    monkeypatch.setenv("LB_ROW_SHAPE", "1")
+    with pytest.raises(lb.LBError) as e:  # the wide shape is FP32 only
+        lb.Lattice(512, 64, _p(lb, lb.LB_F16_DEV, 0))
+    assert e.value.code == lb.LB_EINVAL
+    monkeypatch.delenv("LB_ROW_SHAPE")
+    monkeypatch.setenv("LB_STEP_KERNEL", "tile")
+    lat = lb.Lattice(512, 64, _p(lb, lb.LB_F32, 0))
+    assert lat.row_shape == -1
+    assert lat.autotune(2) == -1
+    lat.close()
