@@ -152,21 +152,33 @@ __global__ void __launch_bounds__(MTH, sizeof(C) == 4 ? 3 : 1)
     }
     const C usq = C(1.5) * (vx * vx + vy * vy);
     const C om = ph.omega[s];
+    C fs[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const C cu = C(Q9::cx(i)) * vx + C(Q9::cy(i)) * vy;
       const C feq = wq<C>(i) * rho[s] * (C(1) + C(3) * cu + C(4.5) * cu * cu - usq);
-      C fs = f[s][i] - om * (f[s][i] - feq);
-      int yd = y + Q9::cy(i);
+      fs[i] = f[s][i] - om * (f[s][i] - feq);
+      const int yd = y + Q9::cy(i);
       if (couette && (yd < 0 || yd >= g.ny)) {
         // Ladd: back along opp(i) at the same site, less 2 w_i rho_s (c_i . U_w)/cs2
         const C Uw = (yd >= g.ny) ? ph.Uwall : -ph.Uwall;
-        fs -= C(6) * wq<C>(i) * rho[s] * C(Q9::cx(i)) * Uw;
-        dst[midx(g, s, Q9::opp(i), y, x)] = fs;
-      } else {
-        yd = wrapi(yd, g.ny);
-        dst[midx(g, s, i, yd, wrapi(x + Q9::cx(i), g.nx))] = fs;
+        fs[i] -= C(6) * wq<C>(i) * rho[s] * C(Q9::cx(i)) * Uw;
       }
+    }
+    if (sizeof(C) == 4) {
+      // FP32: the rest population takes what the eight moving ones leave of
+      // rho_s, so that the collision conserves each species' mass per site up
+      // to one rounding (the nine equilibria, summed in FP32, miss rho_s by a
+      // biased rounding error that drifts the mass by ~1e-8 per step)
+      fs[0] = rho[s] - (((fs[1] + fs[2]) + (fs[3] + fs[4])) + ((fs[5] + fs[6]) + (fs[7] + fs[8])));
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const int yd = y + Q9::cy(i);
+      if (couette && (yd < 0 || yd >= g.ny))
+        dst[midx(g, s, Q9::opp(i), y, x)] = fs[i];
+      else
+        dst[midx(g, s, i, wrapi(yd, g.ny), wrapi(x + Q9::cx(i), g.nx))] = fs[i];
     }
   }
   if (bad) atomicAdd(&status->bad_rho, (unsigned)bad);
