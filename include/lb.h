@@ -154,7 +154,8 @@ LB_API int lb_step(lb_handle *h, int64_t n);
 LB_API int lb_row_shape(const lb_handle *h);
 
 /* Time each available row-kernel shape for steps_per_candidate >= 1 steps
- * (after two untimed ones) and keep the fastest; another shape replaces the
+ * (after two untimed ones; three rounds with the candidates interleaved, the
+ * fastest round counting) and keep the fastest; another shape replaces the
  * current one only if it is at least 1 % faster.  The candidates step from
  * the current state into the handle's other buffer, so the state, the step
  * count and the status word are unchanged.  Synchronises.  *shape (may be

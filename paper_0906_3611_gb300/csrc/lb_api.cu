@@ -280,20 +280,26 @@ extern "C" int lb_autotune(lb_handle* h, int steps_per_candidate, int* shape_out
   const int keep = h->shape;
   const Series keep_sr = h->sr;
   h->sr.buf = nullptr;  // (the candidates' steps are not recorded)
-  float ms[kRowShapes] = {};
+  // three rounds, the candidates interleaved within each; a candidate's time
+  // is its fastest round (short timings on a shared clock are noisy)
+  float ms[kRowShapes];
+  for (int c = 0; c < kRowShapes; ++c) ms[c] = 3.0e38f;
   int rc = LB_OK;
-  for (int c = 0; c < nc && rc == LB_OK; ++c) {
-    h->shape = cand[c];
-    cudaError_t e = cudaSuccess;
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = step_once(h, h->cur, h->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
-    for (int k = 0; k < steps_per_candidate && e == cudaSuccess; ++k)
-      e = step_once(h, h->cur, h->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
-    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[c], e0, e1);
-    if (e != cudaSuccess) rc = LB_ECUDA;
-  }
+  for (int round = 0; round < 3 && rc == LB_OK; ++round)
+    for (int c = 0; c < nc && rc == LB_OK; ++c) {
+      h->shape = cand[c];
+      cudaError_t e = cudaSuccess;
+      for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = step_once(h, h->cur, h->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+      for (int k = 0; k < steps_per_candidate && e == cudaSuccess; ++k)
+        e = step_once(h, h->cur, h->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float t = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+      if (e != cudaSuccess) rc = LB_ECUDA;
+      else if (t < ms[c]) ms[c] = t;
+    }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   h->shape = keep;
