@@ -67,8 +67,10 @@ __global__ void __launch_bounds__(MTH, sizeof(C) == 4 ? 3 : 1)
   // -- densities and pseudo-potentials of every species on the tile + halo 2 --
   for (int e = tid; e < MEX * MEY; e += MTH) {
     const int ex = e % MEX, ey = e / MEX;
-    const int gx = wrapi(x0 + ex - 2, g.nx);
-    const int gy = stencil_row(y0 + ey - 2, g.ny, g.boundary);
+    // (the general wrap, an integer division, only off the lattice's edges)
+    int gx = x0 + ex - 2, gy = y0 + ey - 2;
+    if (gx < 0 || gx >= g.nx) gx = wrapi(gx, g.nx);
+    if (gy < 0 || gy >= g.ny) gy = stencil_row(gy, g.ny, g.boundary);
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       C r = C(0);
@@ -117,6 +119,9 @@ __global__ void __launch_bounds__(MTH, sizeof(C) == 4 ? 3 : 1)
 
   int bad = 0;
   const bool couette = g.boundary == LB_COUETTE;
+  // push targets: columns x-1, x, x+1 and rows y-1, y, y+1, wrapped
+  const int xw[3] = {x == 0 ? g.nx - 1 : x - 1, x, x == g.nx - 1 ? 0 : x + 1};
+  const int yw[3] = {y == 0 ? g.ny - 1 : y - 1, y, y == g.ny - 1 ? 0 : y + 1};
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     // psi stencil over both belts, the twelve opposite pairs as differences:
@@ -178,7 +183,7 @@ __global__ void __launch_bounds__(MTH, sizeof(C) == 4 ? 3 : 1)
       if (couette && (yd < 0 || yd >= g.ny))
         dst[midx(g, s, Q9::opp(i), y, x)] = fs[i];
       else
-        dst[midx(g, s, i, wrapi(yd, g.ny), wrapi(x + Q9::cx(i), g.nx))] = fs[i];
+        dst[midx(g, s, i, yw[Q9::cy(i) + 1], xw[Q9::cx(i) + 1])] = fs[i];
     }
   }
   if (bad) atomicAdd(&status->bad_rho, (unsigned)bad);
