@@ -49,8 +49,10 @@ __global__ void __launch_bounds__(TTHREADS)
   // -- densities and pseudo-potentials on the tile + halo 2 --
   for (int e = tid; e < TEX * TEY; e += TTHREADS) {
     const int ex = e % TEX, ey = e / TEX;
-    const int gx = wrapi(x0 + ex - 2, g.nx);
-    const int gy = stencil_row(y0 + ey - 2, g.ny, g.boundary);
+    // (the general wrap, an integer division, only off the lattice's edges)
+    int gx = x0 + ex - 2, gy = y0 + ey - 2;
+    if (gx < 0 || gx >= g.nx) gx = wrapi(gx, g.nx);
+    if (gy < 0 || gy >= g.ny) gy = stencil_row(gy, g.ny, g.boundary);
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       C dr = C(0);
@@ -198,8 +200,10 @@ __global__ void __launch_bounds__(TTHREADS)
           if (g.boundary == LB_COUETTE && (yd < 0 || yd >= g.ny)) {
             dst[lidx(g, s, Q9::opp(i), y, x)] = S::st(d[s][i]);
           } else {
-            yd = wrapi(yd, g.ny);
-            const int xd = wrapi(x + Q9::cx(i), g.nx);
+            // x +- 1 and y +- 1 wrap by comparison (0 <= x < nx, 0 <= y < ny)
+            const int cx = Q9::cx(i), cy = Q9::cy(i);
+            const int xd = cx == 0 ? x : (cx > 0 ? (x == g.nx - 1 ? 0 : x + 1) : (x == 0 ? g.nx - 1 : x - 1));
+            yd = cy == 0 ? y : (cy > 0 ? (y == g.ny - 1 ? 0 : y + 1) : (y == 0 ? g.ny - 1 : y - 1));
             dst[lidx(g, s, i, yd, xd)] =
                 i == 0 ? store_sr<STORAGE>(d[s][i], s == 0 ? rbits : __funnelshift_l(rbits, rbits, 16)) : S::st(d[s][i]);
           }
