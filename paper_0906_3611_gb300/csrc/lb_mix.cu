@@ -2,7 +2,7 @@
 // species s = 1..N_s (Sec. II) with a symmetric cross-coupling matrix G_ss',
 // and the lb_mix_* entry points of include/lb.h.
 //
-// Fused step kernel on 32 x 8 tiles: the CTA forms rho_s and
+// Fused step kernel on 32 x 16 tiles: the CTA forms rho_s and
 // psi_s = rho0 (1 - exp(-rho_s/rho0)) (Eq. (PSI)) of every species on its
 // tile plus a halo of two sites in shared memory; each thread then takes one
 // site: moments, the common velocity, per species the force
@@ -26,7 +26,8 @@
 namespace lbk {
 namespace {
 
-constexpr int MTX = 32, MTY = 8, MEX = MTX + 4, MEY = MTY + 4, MTH = MTX * MTY;
+// tiles of 32 x 16 sites, 256 threads: each thread takes two sites, rows ty and ty + 8
+constexpr int MTX = 32, MTY = 16, MEX = MTX + 4, MEY = MTY + 4, MTH = 256, MROWS = MTH / MTX;
 constexpr int kObsGrid = 2 * 152;  // blocks of the observables reduction (fixed: a fixed sum order)
 
 struct MixGeom {
@@ -54,7 +55,7 @@ __host__ __device__ __forceinline__ size_t midx(const MixGeom& g, int s, int i, 
   return (size_t)(s * 9 + i) * (size_t)g.plane + (size_t)y * (size_t)g.pitch + (size_t)x;
 }
 
-// One step of every species (src -> dst) on a 32 x 8 tile per CTA.
+// One step of every species (src -> dst) on a 32 x 16 tile per CTA.
 template <int NS, typename C>
 __global__ void __launch_bounds__(MTH, sizeof(C) == 4 ? 3 : 1)
     k_mix(const C* __restrict__ src, C* __restrict__ dst, MixGeom g, MixPhys<C> ph,
@@ -82,108 +83,111 @@ __global__ void __launch_bounds__(MTH, sizeof(C) == 4 ? 3 : 1)
   }
   __syncthreads();
 
-  const int tx = tid % MTX, ty = tid / MTX;
-  const int x = x0 + tx, y = y0 + ty;
-  if (x >= g.nx || y >= g.ny) return;
-
-  C f[NS][9];
-  C rho[NS], jx[NS], jy[NS];
-  C den = C(0), nux = C(0), nuy = C(0);
-#pragma unroll
-  for (int s = 0; s < NS; ++s) {
-#pragma unroll
-    for (int i = 0; i < 9; ++i) f[s][i] = src[midx(g, s, i, y, x)];
-    rho[s] = s_rho[s][ty + 2][tx + 2];
-    jx[s] = (f[s][1] - f[s][3]) + (f[s][5] - f[s][6]) + (f[s][8] - f[s][7]);
-    jy[s] = (f[s][2] - f[s][4]) + (f[s][5] - f[s][8]) + (f[s][6] - f[s][7]);
-    den += rho[s] * ph.omega[s];
-    nux += jx[s] * ph.omega[s];
-    nuy += jy[s] * ph.omega[s];
-  }
-  const C ux = div_c<C>(nux, den), uy = div_c<C>(nuy, den);
-
-  // belt-1 density sums of every species (shared by the pair terms): the
-  // four opposite pairs of belt 1 enter as differences
-  C Xx[NS], Xy[NS];
-#pragma unroll
-  for (int t = 0; t < NS; ++t) {
-    const C(*r)[MEX] = s_rho[t];
-    const int a = ty + 2, b = tx + 2;
-    const C e = r[a][b + 1] - r[a][b - 1];          // (+-1, 0)
-    const C n = r[a + 1][b] - r[a - 1][b];          // (0, +-1)
-    const C d1 = r[a + 1][b + 1] - r[a - 1][b - 1];  // (1, 1) and (-1, -1)
-    const C d2 = r[a + 1][b - 1] - r[a - 1][b + 1];  // (-1, 1) and (1, -1)
-    Xx[t] = wq<C>(1) * e + wq<C>(5) * (d1 - d2);
-    Xy[t] = wq<C>(1) * n + wq<C>(5) * (d1 + d2);
-  }
-
   int bad = 0;
   const bool couette = g.boundary == LB_COUETTE;
-  // push targets: columns x-1, x, x+1 and rows y-1, y, y+1, wrapped
-  const int xw[3] = {x == 0 ? g.nx - 1 : x - 1, x, x == g.nx - 1 ? 0 : x + 1};
-  const int yw[3] = {y == 0 ? g.ny - 1 : y - 1, y, y == g.ny - 1 ? 0 : y + 1};
+  const int tx = tid % MTX;
+#pragma unroll 1
+  for (int ty = tid / MTX; ty < MTY; ty += MROWS) {
+    const int x = x0 + tx, y = y0 + ty;
+    if (x >= g.nx || y >= g.ny) break;
+
+    C f[NS][9];
+    C rho[NS], jx[NS], jy[NS];
+    C den = C(0), nux = C(0), nuy = C(0);
 #pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    // psi stencil over both belts, the twelve opposite pairs as differences:
-    // sum_c W(c) psi(r + c) c = sum over pairs W(c) c [psi(r + c) - psi(r - c)]
-    C sx = C(0), sy = C(0);
-    const C(*q)[MEX] = s_psi[s];
-    const int a = ty + 2, b = tx + 2;
+    for (int s = 0; s < NS; ++s) {
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      const int dx = pair_dx(k), dy = pair_dy(k);
-      const C diff = q[a + dy][b + dx] - q[a - dy][b - dx];
-      if (dx != 0) sx += ph.Wd[s][k][0] * diff;
-      if (dy != 0) sy += ph.Wd[s][k][1] * diff;
+      for (int i = 0; i < 9; ++i) f[s][i] = src[midx(g, s, i, y, x)];
+      rho[s] = s_rho[s][ty + 2][tx + 2];
+      jx[s] = (f[s][1] - f[s][3]) + (f[s][5] - f[s][6]) + (f[s][8] - f[s][7]);
+      jy[s] = (f[s][2] - f[s][4]) + (f[s][5] - f[s][8]) + (f[s][6] - f[s][7]);
+      den += rho[s] * ph.omega[s];
+      nux += jx[s] * ph.omega[s];
+      nuy += jy[s] * ph.omega[s];
     }
-    C fxx = C(0), fxy = C(0);
+    const C ux = div_c<C>(nux, den), uy = div_c<C>(nuy, den);
+
+    // belt-1 density sums of every species (shared by the pair terms): the
+    // four opposite pairs of belt 1 enter as differences
+    C Xx[NS], Xy[NS];
 #pragma unroll
     for (int t = 0; t < NS; ++t) {
-      if (t == s) continue;
-      fxx += ph.gX[s][t] * Xx[t];
-      fxy += ph.gX[s][t] * Xy[t];
+      const C(*r)[MEX] = s_rho[t];
+      const int a = ty + 2, b = tx + 2;
+      const C e = r[a][b + 1] - r[a][b - 1];          // (+-1, 0)
+      const C n = r[a + 1][b] - r[a - 1][b];          // (0, +-1)
+      const C d1 = r[a + 1][b + 1] - r[a - 1][b - 1];  // (1, 1) and (-1, -1)
+      const C d2 = r[a + 1][b - 1] - r[a - 1][b + 1];  // (-1, 1) and (1, -1)
+      Xx[t] = wq<C>(1) * e + wq<C>(5) * (d1 - d2);
+      Xy[t] = wq<C>(1) * n + wq<C>(5) * (d1 + d2);
     }
-    const C pc = s_psi[s][ty + 2][tx + 2];
-    const C Fx = -pc * sx - rho[s] * fxx;
-    const C Fy = -pc * sy - rho[s] * fxy;
-    // shifted velocity v_s = u + tau_s F_s / rho_s (no shift where rho_s <= 0)
-    C vx = ux, vy = uy;
-    if (rho[s] > C(0)) {
-      const C k = div_c<C>(ph.tau[s], rho[s]);
-      vx += k * Fx;
-      vy += k * Fy;
-    } else {
-      ++bad;
-    }
-    const C usq = C(1.5) * (vx * vx + vy * vy);
-    const C om = ph.omega[s];
-    C fs[9];
+
+    // push targets: columns x-1, x, x+1 and rows y-1, y, y+1, wrapped
+    const int xw[3] = {x == 0 ? g.nx - 1 : x - 1, x, x == g.nx - 1 ? 0 : x + 1};
+    const int yw[3] = {y == 0 ? g.ny - 1 : y - 1, y, y == g.ny - 1 ? 0 : y + 1};
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const C cu = C(Q9::cx(i)) * vx + C(Q9::cy(i)) * vy;
-      const C feq = wq<C>(i) * rho[s] * (C(1) + C(3) * cu + C(4.5) * cu * cu - usq);
-      fs[i] = f[s][i] - om * (f[s][i] - feq);
-      const int yd = y + Q9::cy(i);
-      if (couette && (yd < 0 || yd >= g.ny)) {
-        // Ladd: back along opp(i) at the same site, less 2 w_i rho_s (c_i . U_w)/cs2
-        const C Uw = (yd >= g.ny) ? ph.Uwall : -ph.Uwall;
-        fs[i] -= C(6) * wq<C>(i) * rho[s] * C(Q9::cx(i)) * Uw;
+    for (int s = 0; s < NS; ++s) {
+      // psi stencil over both belts, the twelve opposite pairs as differences:
+      // sum_c W(c) psi(r + c) c = sum over pairs W(c) c [psi(r + c) - psi(r - c)]
+      C sx = C(0), sy = C(0);
+      const C(*q)[MEX] = s_psi[s];
+      const int a = ty + 2, b = tx + 2;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const int dx = pair_dx(k), dy = pair_dy(k);
+        const C diff = q[a + dy][b + dx] - q[a - dy][b - dx];
+        if (dx != 0) sx += ph.Wd[s][k][0] * diff;
+        if (dy != 0) sy += ph.Wd[s][k][1] * diff;
       }
-    }
-    if (sizeof(C) == 4) {
-      // FP32: the rest population takes what the eight moving ones leave of
-      // rho_s, so that the collision conserves each species' mass per site up
-      // to one rounding (the nine equilibria, summed in FP32, miss rho_s by a
-      // biased rounding error that drifts the mass by ~1e-8 per step)
-      fs[0] = rho[s] - (((fs[1] + fs[2]) + (fs[3] + fs[4])) + ((fs[5] + fs[6]) + (fs[7] + fs[8])));
-    }
+      C fxx = C(0), fxy = C(0);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const int yd = y + Q9::cy(i);
-      if (couette && (yd < 0 || yd >= g.ny))
-        dst[midx(g, s, Q9::opp(i), y, x)] = fs[i];
-      else
-        dst[midx(g, s, i, yw[Q9::cy(i) + 1], xw[Q9::cx(i) + 1])] = fs[i];
+      for (int t = 0; t < NS; ++t) {
+        if (t == s) continue;
+        fxx += ph.gX[s][t] * Xx[t];
+        fxy += ph.gX[s][t] * Xy[t];
+      }
+      const C pc = s_psi[s][ty + 2][tx + 2];
+      const C Fx = -pc * sx - rho[s] * fxx;
+      const C Fy = -pc * sy - rho[s] * fxy;
+      // shifted velocity v_s = u + tau_s F_s / rho_s (no shift where rho_s <= 0)
+      C vx = ux, vy = uy;
+      if (rho[s] > C(0)) {
+        const C k = div_c<C>(ph.tau[s], rho[s]);
+        vx += k * Fx;
+        vy += k * Fy;
+      } else {
+        ++bad;
+      }
+      const C usq = C(1.5) * (vx * vx + vy * vy);
+      const C om = ph.omega[s];
+      C fs[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const C cu = C(Q9::cx(i)) * vx + C(Q9::cy(i)) * vy;
+        const C feq = wq<C>(i) * rho[s] * (C(1) + C(3) * cu + C(4.5) * cu * cu - usq);
+        fs[i] = f[s][i] - om * (f[s][i] - feq);
+        const int yd = y + Q9::cy(i);
+        if (couette && (yd < 0 || yd >= g.ny)) {
+          // Ladd: back along opp(i) at the same site, less 2 w_i rho_s (c_i . U_w)/cs2
+          const C Uw = (yd >= g.ny) ? ph.Uwall : -ph.Uwall;
+          fs[i] -= C(6) * wq<C>(i) * rho[s] * C(Q9::cx(i)) * Uw;
+        }
+      }
+      if (sizeof(C) == 4) {
+        // FP32: the rest population takes what the eight moving ones leave of
+        // rho_s, so that the collision conserves each species' mass per site up
+        // to one rounding (the nine equilibria, summed in FP32, miss rho_s by a
+        // biased rounding error that drifts the mass by ~1e-8 per step)
+        fs[0] = rho[s] - (((fs[1] + fs[2]) + (fs[3] + fs[4])) + ((fs[5] + fs[6]) + (fs[7] + fs[8])));
+      }
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const int yd = y + Q9::cy(i);
+        if (couette && (yd < 0 || yd >= g.ny))
+          dst[midx(g, s, Q9::opp(i), y, x)] = fs[i];
+        else
+          dst[midx(g, s, i, yw[Q9::cy(i) + 1], xw[Q9::cx(i) + 1])] = fs[i];
+      }
     }
   }
   if (bad) atomicAdd(&status->bad_rho, (unsigned)bad);
