@@ -43,6 +43,10 @@ struct MixPhys {
   C Wpsi[LB_MAX_SPECIES][5];            // G^a_s w_k + G^r_s p_k per |c|^2 group (1, 2, 4, 5, 8)
   C gX[LB_MAX_SPECIES][LB_MAX_SPECIES];  // G_ss' / rho0^2 (zero on the diagonal)
   C Wd[LB_MAX_SPECIES][12][2];           // Wpsi of pair k times its (c_x, c_y) (see kMixPairs)
+  // the collision's constants per species: 1 - omega_s and omega_s times the
+  // D2Q9 weights w_0, w_1, w_5, 3 w_1, 4.5 w_1, 3 w_5, 4.5 w_5
+  C keep[LB_MAX_SPECIES];
+  C ow[LB_MAX_SPECIES][7];
   C Uwall;
 };
 
@@ -158,14 +162,30 @@ __global__ void __launch_bounds__(MTH, sizeof(C) == 4 ? 3 : 1)
       } else {
         ++bad;
       }
-      const C usq = C(1.5) * (vx * vx + vy * vy);
-      const C om = ph.omega[s];
+      // f*_i = (1 - omega) f_i + omega f^eq_i with omega f^eq_i =
+      // omega w_i rho [1 + 3 c_i.v + 4.5 (c_i.v)^2 - 1.5 v^2], evaluated once
+      // per pair of opposite directions: the even part (the rest term and the
+      // square) is shared, the odd part (3 c_i.v) changes sign
+      const C tt = rho[s] * (C(1) - C(1.5) * (vx * vx + vy * vy));
+      const C kp = ph.keep[s];
+      const C B0 = ph.ow[s][0] * tt, B1 = ph.ow[s][1] * tt, B2 = ph.ow[s][2] * tt;
+      const C a1 = ph.ow[s][3] * rho[s], b1 = ph.ow[s][4] * rho[s];
+      const C a2 = ph.ow[s][5] * rho[s], b2 = ph.ow[s][6] * rho[s];
+      const C s1 = vx + vy, s2 = vx - vy;
+      const C ex = B1 + b1 * vx * vx, ax = a1 * vx, ey = B1 + b1 * vy * vy, ay = a1 * vy;
+      const C e1 = B2 + b2 * s1 * s1, ad1 = a2 * s1, e2 = B2 + b2 * s2 * s2, ad2 = a2 * s2;
       C fs[9];
+      fs[0] = kp * f[s][0] + B0;
+      fs[1] = kp * f[s][1] + (ex + ax);
+      fs[3] = kp * f[s][3] + (ex - ax);
+      fs[2] = kp * f[s][2] + (ey + ay);
+      fs[4] = kp * f[s][4] + (ey - ay);
+      fs[5] = kp * f[s][5] + (e1 + ad1);
+      fs[7] = kp * f[s][7] + (e1 - ad1);
+      fs[8] = kp * f[s][8] + (e2 + ad2);
+      fs[6] = kp * f[s][6] + (e2 - ad2);
 #pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        const C cu = C(Q9::cx(i)) * vx + C(Q9::cy(i)) * vy;
-        const C feq = wq<C>(i) * rho[s] * (C(1) + C(3) * cu + C(4.5) * cu * cu - usq);
-        fs[i] = f[s][i] - om * (f[s][i] - feq);
+      for (int i = 1; i < 9; ++i) {
         const int yd = y + Q9::cy(i);
         if (couette && (yd < 0 || yd >= g.ny)) {
           // Ladd: back along opp(i) at the same site, less 2 w_i rho_s (c_i . U_w)/cs2
@@ -293,6 +313,10 @@ MixPhys<C> make_mix_phys(const lb_mix_params& p) {
       m.Wd[s][k][1] = (C)(wk * dy);
     }
     for (int t = 0; t < p.ns; ++t) m.gX[s][t] = (C)(t == s ? 0.0 : p.G[s][t] / r2);
+    const double om = 1.0 / p.tau[s];
+    m.keep[s] = (C)(1.0 - om);
+    const double wf[7] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 36.0, 3.0 / 9.0, 4.5 / 9.0, 3.0 / 36.0, 4.5 / 36.0};
+    for (int k = 0; k < 7; ++k) m.ow[s][k] = (C)(om * wf[k]);
   }
   m.rho0 = (C)p.rho0;
   m.inv_rho0 = (C)(1.0 / p.rho0);
