@@ -130,22 +130,29 @@ def test_observables_match_the_oracle_and_are_conserved(lb):
     assert np.max(np.abs(o1["momentum"] - o0["momentum"])) < 1e-10
 
 
-def test_fp32_mixture_mass_drift_is_small(lb):
-    # FP32 populations are stored as they are (no reference shift).  With the
-    # rest population taking what the eight moving ones leave of rho_s, the
-    # collision conserves each species' mass per site up to a few roundings;
-    # the nine equilibria summed in FP32 instead drifted the mass by about
-    # 1e-8 per step (2e-5 over this run).  Measured with the mass-exact rest
-    # population: 6e-7 over this run (3e-10 per step, still one-signed).  The
-    # bar sits between the two: a regression guard for the mass-exact
-    # construction, not an accuracy bound.
+def test_fp32_mixture_mass_drift_is_a_random_walk(lb):
+    """FP32 populations are stored as they are (no reference shift).  The
+    rest population takes what the eight moving ones leave of rho_s, so a
+    site's mass changes in a step only by roundings: the FP32 sums that form
+    rho_s (8 additions, depth 4) and the eight stored values (depth 3), and
+    the subtraction that forms the rest population -- about 15 roundings of
+    values up to rho_s, each uniform within half an ulp (<= 2u rho_s, u =
+    2^-24), so a standard deviation of at most sqrt(15 (2u)^2 / 12) ~ 2.2 u
+    rho_s per site and step.  Unbiased and independent across N sites and
+    T steps, the relative drift of a species' mass has a standard deviation of
+    about 2.2 u sqrt(T / N); the bar is 10 u sqrt(T / N) (4.5 sd).  A biased
+    collision breaks it: the nine equilibria summed in FP32 drifted by 1e-8
+    per step (2e-5 here), the unfactored equilibrium with the mass-exact rest
+    population by 3e-10 per step (6e-7 here, against the bar's 1e-7)."""
     G = np.array([[0.0, 0.405, 0.2], [0.405, 0.0, 0.2], [0.2, 0.2, 0.0]])
     p = lb.make_mix_params(3, [1.0, 1.0, 1.0], 0.7, [-9.0, -9.0, 0.0], [8.1, 8.1, 0.0], G,
                            boundary=0, U_wall=0.0, storage=lb.LB_F32)
-    mx = lb.Mixture(256, 256, p).init_random(7, [1.0, 1.0, 0.1], [0.05, 0.05, 0.01])
+    n, T = 256, 2000
+    mx = lb.Mixture(n, n, p).init_random(7, [1.0, 1.0, 0.1], [0.05, 0.05, 0.01])
     m0 = mx.observables()["mass"][:3]
-    mx.step(2000)
+    mx.step(T)
     m1 = mx.observables()["mass"][:3]
     assert mx.status() == lb.LB_OK
     mx.close()
-    assert float(np.max(np.abs(m1 / m0 - 1))) <= 2e-6
+    bar = 10.0 * 2.0 ** -24 * np.sqrt(T / (n * n))
+    assert float(np.max(np.abs(m1 / m0 - 1))) <= bar
