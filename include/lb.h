@@ -142,15 +142,16 @@ LB_API int lb_init_random(lb_handle *h, uint64_t seed);
 LB_API int lb_step(lb_handle *h, int64_t n);
 
 /* CTA shape of the row-streaming step kernel: 0 (every storage: 4 compute
- * warps on 128-column strips) or 1 (FP32 only: 7 compute warps on 224-column
- * strips, two CTAs per SM -- fewer halo columns per site, faster on large
- * lattices, slower on small ones); -1 when the lattice is stepped by the
- * generic tile kernel.  The shape changes how the lattice is cut into CTA
- * work, not the arithmetic: every shape gives the same bits.  lb_create()
- * chooses it by timing the candidates (lb_autotune with 8 steps each) on
- * FP32 lattices of at least 2^22 sites, else takes shape 0; the environment
- * variable LB_ROW_SHAPE=0|1, read by lb_create(), forces one (LB_EINVAL if
- * it does not apply). */
+ * warps on 128-column strips) or 1 (not FP64: FP32 7 compute warps on
+ * 224-column strips, the 16-bit storages 8 on 256-column strips, two CTAs per
+ * SM -- fewer halo columns per site, faster on large lattices, slower on
+ * small ones); -1 when the lattice is stepped by the generic tile kernel.
+ * The shape changes how the lattice is cut into CTA work, not the
+ * arithmetic: every shape gives the same bits.  lb_create() chooses it by
+ * timing the candidates (lb_autotune with 8 steps each) on lattices of at
+ * least 2^22 sites in the deviation storages, else takes shape 0; the
+ * environment variable LB_ROW_SHAPE=0|1, read by lb_create(), forces one
+ * (LB_EINVAL if it does not apply). */
 LB_API int lb_row_shape(const lb_handle *h);
 
 /* Time each available row-kernel shape for steps_per_candidate >= 1 steps

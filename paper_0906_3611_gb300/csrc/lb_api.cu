@@ -138,9 +138,9 @@ static int create_common(int nx, int ny, const lb_params* p, void* stream, void*
     h->use_rows = 1;
   } else
     h->use_rows = (rows_ok && nx >= 128) ? 1 : 0;
-  // the row kernel's CTA shape: LB_ROW_SHAPE forces one; large FP32 lattices
-  // time the candidates on the zeroed buffers (deviation storage: the uniform
-  // rest state rho_ref, no non-positive densities)
+  // the row kernel's CTA shape: LB_ROW_SHAPE forces one; large lattices in
+  // the deviation storages time the candidates on the zeroed buffers (the
+  // uniform rest state rho_ref, no non-positive densities)
   const char* shape = getenv("LB_ROW_SHAPE");
   if (shape && *shape) {
     h->shape = atoi(shape);
@@ -149,7 +149,7 @@ static int create_common(int nx, int ny, const lb_params* p, void* stream, void*
       lb_destroy(h);
       return LB_EINVAL;
     }
-  } else if (h->use_rows && !h->stall && p->storage == LB_F32 &&
+  } else if (h->use_rows && !h->stall && p->storage != LB_F64 &&
              (long long)nx * ny >= (1LL << 22)) {
     rc = lb_autotune(h, 8, nullptr);
     if (rc) {

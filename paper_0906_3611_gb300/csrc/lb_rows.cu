@@ -63,7 +63,14 @@ static int resident_blocks() {
 }
 
 static int resident(int storage, int shape = 0) {
-  if (shape == 1) return storage == LB_F32 ? resident_blocks<row_key(LB_F32, 1)>() : 0;
+  if (shape == 1) {
+    switch (storage) {
+      case LB_F32: return resident_blocks<row_key(LB_F32, 1)>();
+      case LB_BF16_DEV: return resident_blocks<row_key(LB_BF16_DEV, 1)>();
+      case LB_F16_DEV: return resident_blocks<row_key(LB_F16_DEV, 1)>();
+    }
+    return 0;
+  }
   if (shape != 0) return 0;
   switch (storage) {
     case LB_F64: return resident_blocks<LB_F64>();
@@ -162,8 +169,14 @@ cudaError_t launch_step_rows(int storage, int shape, const void* src, void* dst,
                              const PhysD& ph, const void* body, Status* status, const Series& sr,
                              int stall, cudaStream_t st) {
   if (shape == 1) {
-    if (storage != LB_F32) return cudaErrorInvalidValue;
-    return rows_t<row_key(LB_F32, 1)>(src, dst, g, ph, body, status, sr, stall, st);
+    switch (storage) {
+      case LB_F32: return rows_t<row_key(LB_F32, 1)>(src, dst, g, ph, body, status, sr, stall, st);
+      case LB_BF16_DEV:
+        return rows_t<row_key(LB_BF16_DEV, 1)>(src, dst, g, ph, body, status, sr, stall, st);
+      case LB_F16_DEV:
+        return rows_t<row_key(LB_F16_DEV, 1)>(src, dst, g, ph, body, status, sr, stall, st);
+    }
+    return cudaErrorInvalidValue;
   }
   if (shape != 0) return cudaErrorInvalidValue;
   switch (storage) {

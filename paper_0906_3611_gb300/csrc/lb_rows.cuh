@@ -91,6 +91,19 @@ struct RowsCfg<LB_F16_DEV> {
   static constexpr int NCW = 4, SOFF = 4, NSLOT = 8, MINB = 4;
   static constexpr bool PIPE = false, LAG = true, LAG_BATCH = true, CPAR = true;
 };
+// the wide 16-bit shapes: 8 compute warps on 256-column strips, 2 CTAs per SM
+// (the same 16 compute warps per SM with half the staging warps and half the
+// halo columns per site)
+template <>
+struct RowsCfg<row_key(LB_BF16_DEV, 1)> {
+  static constexpr int NCW = 8, SOFF = 4, NSLOT = 8, MINB = 2;
+  static constexpr bool PIPE = false, LAG = true, LAG_BATCH = true, CPAR = true;
+};
+template <>
+struct RowsCfg<row_key(LB_F16_DEV, 1)> {
+  static constexpr int NCW = 8, SOFF = 4, NSLOT = 8, MINB = 2;
+  static constexpr bool PIPE = false, LAG = true, LAG_BATCH = true, CPAR = true;
+};
 
 template <int STORAGE>
 constexpr int strip_cols() {

@@ -37,10 +37,12 @@ struct WorkItem {
 };
 
 // CTA shapes of the single-lattice row kernel.  Shape 0 is every storage's
-// default: 4 compute warps on 128-column strips.  Shape 1, FP32 only: 7
-// compute warps on 224-column strips, 2 CTAs per SM instead of 3 (fewer halo
-// columns per site: faster on large lattices, slower on small ones).  Kernel
-// instantiations are keyed by storage | shape << 2.
+// default: 4 compute warps on 128-column strips.  Shape 1 (not FP64): FP32 7
+// compute warps on 224-column strips, 2 CTAs per SM instead of 3; the 16-bit
+// storages 8 compute warps on 256-column strips, 2 CTAs per SM instead of 4
+// (fewer halo columns per site and staging warps per SM: faster on large
+// lattices, slower on small ones).  Kernel instantiations are keyed by
+// storage | shape << 2.
 constexpr int kRowShapes = 2;
 constexpr int row_key(int storage, int shape) { return storage | (shape << 2); }
 constexpr int row_storage(int key) { return key & 3; }

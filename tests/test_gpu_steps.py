@@ -6,9 +6,9 @@ every step alone; run as a batch replica, it goes through the batched
 kernel, which splits the rows into other work items.  The per-site
 arithmetic does not depend on any of this, so all three must agree bit for
 bit, across graph boundaries, odd step counts and the buffer parity they
-leave, in every storage and for both boundaries.  The FP32 row kernel's two
-CTA shapes cut the lattice into different strips and ranges and give the
-same bits too; the shape autotuner leaves the state, the step count and the
+leave, in every storage and for both boundaries.  The row kernel's two CTA
+shapes (FP32 and the 16-bit storages) cut the lattice into different strips
+and ranges and give the same bits too; the shape autotuner leaves the state, the step count and the
 status word as they were.
 """
 import numpy as np
@@ -64,10 +64,13 @@ def test_one_call_equals_single_steps_and_the_batched_kernel(lb, monkeypatch, st
 
 @pytest.mark.parametrize("boundary", [0, 1], ids=["periodic", "couette"])
 @pytest.mark.parametrize("nx", [500, 1024])
-def test_the_wide_cta_shape_gives_the_same_bits(lb, monkeypatch, nx, boundary):
-    # FP32 shape 1 (224-column strips, 7 compute warps) against shape 0
-    # (128-column strips); nx = 500 leaves a ragged last strip in both
-    p = _p(lb, lb.LB_F32, boundary)
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_the_wide_cta_shape_gives_the_same_bits(lb, monkeypatch, storage, nx, boundary):
+    # shape 1 (FP32: 224-column strips of 7 compute warps; 16-bit: 256-column
+    # strips of 8) against shape 0 (128-column strips of 4); nx = 500 leaves a
+    # ragged last strip in both
+    st = {"f32": lb.LB_F32, "f16": lb.LB_F16_DEV, "bf16": lb.LB_BF16_DEV}[storage]
+    p = _p(lb, st, boundary)
     ny, n = 96, 45
     out = []
     for shape in ("0", "1"):
@@ -98,8 +101,8 @@ def test_autotune_keeps_the_state_and_reports_the_shape(lb, monkeypatch):
 
 def test_shape_forcing_and_the_tile_kernel(lb, monkeypatch):
     monkeypatch.setenv("LB_ROW_SHAPE", "1")
-    with pytest.raises(lb.LBError) as e:  # the wide shape is FP32 only
-        lb.Lattice(512, 64, _p(lb, lb.LB_F16_DEV, 0))
+    with pytest.raises(lb.LBError) as e:  # no wide shape for FP64
+        lb.Lattice(512, 64, _p(lb, lb.LB_F64, 0))
     assert e.value.code == lb.LB_EINVAL
     monkeypatch.delenv("LB_ROW_SHAPE")
     monkeypatch.setenv("LB_STEP_KERNEL", "tile")
