@@ -152,6 +152,7 @@ static int create_common(int nx, int ny, const lb_params* p, void* stream, void*
   } else if (h->use_rows && !h->stall && p->storage != LB_F64 &&
              (long long)nx * ny >= (1LL << 22)) {
     rc = lb_autotune(h, 8, nullptr);
+    if (rc == LB_EBUSY) rc = LB_OK;  // (a stream being captured: keep shape 0)
     if (rc) {
       lb_destroy(h);
       return rc;
@@ -265,6 +266,13 @@ extern "C" int lb_autotune(lb_handle* h, int steps_per_candidate, int* shape_out
   for (int s = 0; s < kRowShapes; ++s)
     if (rows_shape_available(h->p.storage, s)) cand[nc++] = s;
   if (nc < 2) return LB_OK;
+  // timing needs the stream to run: not while it is being captured into a graph
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(h->stream, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return LB_ECUDA;
+  }
+  if (cs != cudaStreamCaptureStatusNone) return LB_EBUSY;
   // the status word is kept: read it, and write it back after the candidates
   Status saved;
   if (cudaMemcpyAsync(&saved, h->d_status, sizeof(Status), cudaMemcpyDeviceToHost, h->stream) !=
