@@ -150,7 +150,7 @@ def test_couette_without_couplings_matches_the_closed_form(lb, monkeypatch, kern
     assert e_st <= b_st
 
 
-# ---- the survey-size cross-checks: 256 x 256, 10^4 steps (emulsion) and
+# ---- the long cross-checks: 256 x 256, 10^4 steps (emulsion) and
 # 5 x 10^3 steps per wall speed (Couette), against the oracle run on the
 # host cores ----
 #
