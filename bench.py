@@ -648,7 +648,7 @@ def batch_measure(lb, D, name, steps, warmup, reps=5, target_s=None, clocks=None
     budget = 1 << 40  # effectively unbounded: every replica steps in every launch
     for side, U, seed in reps_list:
         b.add(side, side, prm(U), seed, budget)
-    layout, rows = b.autotune(2)
+    layout, rows = b.autotune(6)  # (6 timed steps per candidate: two were within noise)
     b.run(warmup)
     stream.synchronize()
     ms = timed_blocks(D, stream, lambda: b.run(steps), reps, clocks, target_s)
