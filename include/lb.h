@@ -160,8 +160,9 @@ LB_API int lb_row_shape(const lb_handle *h);
  * current one only if it is at least 1 % faster.  The candidates step from
  * the current state into the handle's other buffer, so the state, the step
  * count and the status word are unchanged.  Synchronises.  *shape (may be
- * NULL) receives the choice.  A lattice with one candidate returns at once;
- * LB_EBUSY (nothing changed) while the handle's stream is being captured. */
+ * NULL) receives the choice.  A lattice stepped by the tile kernel returns
+ * at once; LB_EBUSY (nothing changed) while the handle's stream is being
+ * captured. */
 LB_API int lb_autotune(lb_handle *h, int steps_per_candidate, int *shape);
 
 /* Observables of the current state f(t), FP64 on the device; synchronises.

@@ -262,10 +262,6 @@ extern "C" int lb_autotune(lb_handle* h, int steps_per_candidate, int* shape_out
   if (!h || steps_per_candidate < 1) return LB_EINVAL;
   if (shape_out) *shape_out = lb_row_shape(h);
   if (!h->use_rows) return LB_OK;
-  int cand[kRowShapes], nc = 0;
-  for (int s = 0; s < kRowShapes; ++s)
-    if (rows_shape_available(h->p.storage, s)) cand[nc++] = s;
-  if (nc < 2) return LB_OK;
   // timing needs the stream to run: not while it is being captured into a graph
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(h->stream, &cs) != cudaSuccess) {
@@ -273,6 +269,10 @@ extern "C" int lb_autotune(lb_handle* h, int steps_per_candidate, int* shape_out
     return LB_ECUDA;
   }
   if (cs != cudaStreamCaptureStatusNone) return LB_EBUSY;
+  int cand[kRowShapes], nc = 0;
+  for (int s = 0; s < kRowShapes; ++s)
+    if (rows_shape_available(h->p.storage, s)) cand[nc++] = s;
+  if (nc < 2) return LB_OK;
   // the status word is kept: read it, and write it back after the candidates
   Status saved;
   if (cudaMemcpyAsync(&saved, h->d_status, sizeof(Status), cudaMemcpyDeviceToHost, h->stream) !=

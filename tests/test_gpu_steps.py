@@ -110,3 +110,23 @@ def test_shape_forcing_and_the_tile_kernel(lb, monkeypatch):
     assert lat.row_shape == -1
     assert lat.autotune(2) == -1
     lat.close()
+
+
+def test_autotune_refuses_while_the_stream_is_captured(lb, monkeypatch):
+    import torch
+
+    monkeypatch.setenv("LB_STEP_KERNEL", "rows")
+    lat = lb.Lattice(640, 200, _p(lb, lb.LB_F32, 1)).init_random(2)
+    lat.sync()
+    shape = lat.row_shape
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=lat.stream):
+        x = torch.zeros(4, device="cuda")
+        x += 1.0
+        with pytest.raises(lb.LBError) as e:
+            lat.autotune(2)
+    assert e.value.code == lb.LB_EBUSY
+    g.replay()
+    torch.cuda.synchronize()
+    assert lat.row_shape == shape and lat.status() == lb.LB_OK
+    lat.close()
