@@ -316,7 +316,7 @@ extern "C" int lb_autotune(lb_handle* h, int steps_per_candidate, int* shape_out
     cudaGetLastError();
     return rc;
   }
-  int best = -1;
+  int best = 0;  // (the incumbent, which is always a candidate)
   for (int c = 0; c < nc; ++c)
     if (cand[c] == keep) best = c;
   for (int c = 0; c < nc; ++c)
