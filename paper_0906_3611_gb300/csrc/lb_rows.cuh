@@ -386,8 +386,16 @@ struct RowsLoop {
     bad = 0;
   }
 
-  __device__ __forceinline__ int slot_of(int j) const { return (ring + j) % NSLOT; }
-  __device__ __forceinline__ uint32_t round_of(int j) const { return (uint32_t)((ring + j) / NSLOT); }
+  // (ring + j >= 0.  A power-of-two ring, the 16-bit storages', takes the
+  // unsigned form -- a mask and a shift; FP16 +1.3 % -- the FP32 rings of 7
+  // and 6 slots keep the signed one, which measured 2 % faster at 1024^2.)
+  static constexpr bool POW2 = (NSLOT & (NSLOT - 1)) == 0;
+  __device__ __forceinline__ int slot_of(int j) const {
+    return POW2 ? (int)((uint32_t)(ring + j) % NSLOT) : (ring + j) % NSLOT;
+  }
+  __device__ __forceinline__ uint32_t round_of(int j) const {
+    return POW2 ? (uint32_t)(ring + j) / NSLOT : (uint32_t)((ring + j) / NSLOT);
+  }
 
   // ---- the staging warp: stage rows 0 .. nstage-1, each into a slot that
   // every compute warp has released.  `stall` (a test hook for the timeout
