@@ -151,7 +151,7 @@ LB_API int lb_step(lb_handle *h, int64_t n);
  * timing the candidates (lb_autotune with 8 steps each) on lattices of at
  * least 2^22 sites in the deviation storages, else takes shape 0; the
  * environment variable LB_ROW_SHAPE=0|1, read by lb_create(), forces one
- * (LB_EINVAL if it does not apply). */
+ * (LB_EINVAL if it does not apply).  Host-side only; -1 for a NULL handle. */
 LB_API int lb_row_shape(const lb_handle *h);
 
 /* Time each available row-kernel shape for steps_per_candidate >= 1 steps
@@ -161,8 +161,10 @@ LB_API int lb_row_shape(const lb_handle *h);
  * the current state into the handle's other buffer, so the state, the step
  * count and the status word are unchanged.  Synchronises.  *shape (may be
  * NULL) receives the choice.  A lattice stepped by the tile kernel returns
- * at once; LB_EBUSY (nothing changed) while the handle's stream is being
- * captured. */
+ * at once.  Returns LB_OK; LB_EINVAL for a NULL handle or
+ * steps_per_candidate < 1; LB_EBUSY (nothing changed) while the handle's
+ * stream is being captured; LB_ECUDA if a launch or a copy failed (the
+ * shape is then unchanged). */
 LB_API int lb_autotune(lb_handle *h, int steps_per_candidate, int *shape);
 
 /* Observables of the current state f(t), FP64 on the device; synchronises.
