@@ -70,7 +70,8 @@ def test_state_bytes_and_validation_without_gpu(lib):
 
 def test_invalid_arguments_of_the_newer_calls_without_gpu(lib):
     """NULL handles and out-of-range arguments are refused before any device
-    work (shear, response record, bursts, overlap, batch layout and state)."""
+    work (shear, response record, bursts, overlap, batch layout and state, the
+    row-kernel shape calls)."""
     from paper_0906_3611_gb300 import lb
     E = lb.LB_EINVAL
     d = ctypes.c_double()
@@ -89,6 +90,9 @@ def test_invalid_arguments_of_the_newer_calls_without_gpu(lib):
     assert lib.lb_batch_series_read(None, 0, ctypes.byref(d), 1, ctypes.byref(n)) == E
     assert lib.lb_batch_series_stop(None, 0) == E
     assert lib.lb_batch_series_bursts(None, 0, ctypes.c_double(2.0), 4, hist, ctypes.byref(n)) == E
+    shape = ctypes.c_int(7)
+    assert lib.lb_row_shape(None) == -1
+    assert lib.lb_autotune(None, 8, ctypes.byref(shape)) == E and shape.value == 7
     h = ctypes.c_void_p()
     for bad in (lb.make_params(g_kolmo=1e-3, k_kolmo=0), lb.make_params(g_kolmo=float("nan"))):
         assert lib.lb_create(64, 64, ctypes.byref(bad), None, ctypes.byref(h)) == E
