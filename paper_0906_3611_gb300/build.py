@@ -51,13 +51,39 @@ ROWS_SOURCES = ("lb_common.cuh", "lb_pair.cuh", "lb_site.cuh", "lb_kernels.h", "
                 "lb_rows.cuh", "lb_rows.cu", "lb_rows_batch.cu")
 
 
+def _code_only(text: str) -> str:
+    """C/C++ source without its comments and trailing blanks (a comment edit
+    leaves the compiled kernels, and so their profiles, unchanged)."""
+    import re
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c == '"' or c == "'":  # a string or character literal, kept whole
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    lines = [ln.rstrip() for ln in "".join(out).split("\n")]
+    return "\n".join(ln for ln in lines if ln)
+
+
 def rows_kernel_sha() -> str:
-    """Short hash of the row-streaming kernels' sources."""
+    """Short hash of the row-streaming kernels' sources, comments left out."""
     import hashlib
     h = hashlib.sha256()
     for name in ROWS_SOURCES:
         h.update(name.encode())
-        h.update(open(os.path.join(CSRC, name), "rb").read())
+        h.update(_code_only(open(os.path.join(CSRC, name), encoding="utf-8").read()).encode())
     return h.hexdigest()[:12]
 
 

@@ -2,8 +2,9 @@
 // per-CTA row loop shared by the single-lattice kernel (lb_rows.cu) and the
 // batched kernel (lb_rows_batch.cu).
 //
-// Each CTA owns a strip of 32 NCW columns [x0, x1) (128 for every storage)
-// and a contiguous range of rows, and walks down the rows once.  Row r of the
+// Each CTA owns a strip of 32 NCW columns [x0, x1) (128 in every storage's
+// default shape; 224 or 256 in the wide ones) and a contiguous range of rows,
+// and walks down the rows once.  Row r of the
 // state f(t) (the 9 direction planes, both species of each site side by side,
 // columns x0-SOFF .. x1+SOFF-1, periodic in x) is staged in shared memory by bulk
 // asynchronous copies (the TMA engine, cp.async.bulk) into a ring of NSLOT
